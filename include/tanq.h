@@ -1,0 +1,228 @@
+/*
+ * tanq.h -- C ABI of a GB300 (sm_103a) noisy density-matrix simulator.
+ *
+ * The library computes, on one GPU, the problem of TANQ-Sim (arXiv
+ * 2404.13184) Sec. 2.1, Eq. 2: given an n-qubit density matrix rho_in and a
+ * sequence of gates and noise channels G_0 .. G_{m-1},
+ *     rho_out = G_{m-1}( ... G_1(G_0 rho_in G_0^dag) G_1^dag ... ) G_{m-1}^dag,
+ * where a noisy G is a Kraus set {K_i} acting as rho -> sum_i K_i rho K_i^dag
+ * (Sec. 3.1, Kraus sum).
+ *
+ * Method (Sec. 3.1, Eq. "sp"): rho is stored as vec(rho), the column-stacked
+ * 4^n vector (vec index v = r + c * 2^n for rho[r][c]); every op becomes the
+ * superoperator S = sum_i conj(K_i) (x) K_i; consecutive ops are fused into
+ * dense superoperators on at most 4 qubits (Sec. 3.3, generalised); each
+ * fused block is applied to all 4^n entries by gathering the 4^k entries of
+ * every group at the target bit positions (q_j and q_j + n), multiplying by
+ * the 4^k x 4^k superoperator and scattering back (Sec. 3.1, C1/C2 update,
+ * generalised from k = 1, 2 to k <= 4).
+ *
+ * Conventions used by every entry point:
+ *  - qubit q is bit q of the row index r and of the column index c, so it is
+ *    bits q and q + n of the vec index;
+ *  - a k-qubit matrix acts on an ordered list qubits[0..k-1]; bit j of its
+ *    local row/column index is qubit qubits[j] (qubits[0] is the least
+ *    significant local bit);
+ *  - matrices are 2^k x 2^k complex, row-major, interleaved (re, im) doubles:
+ *    element (i, j) is at [2*(i*2^k + j)] (re) and [2*(i*2^k + j) + 1] (im);
+ *  - readouts are reduced in FP64 in a fixed order (deterministic for a given
+ *    n and precision).
+ *
+ * Ownership: every input array is owned by the caller and copied (or fully
+ * consumed) before the call returns; output arrays are caller-allocated. A
+ * tq_state owns its device buffers until tq_free (except for the rho buffer
+ * passed to tq_create_on, which stays the caller's).
+ *
+ * Streams: apply calls enqueue work on the state's CUDA stream and return
+ * without waiting; readouts (tq_trace, tq_expect_z, tq_probs, tq_get_rho)
+ * wait for the stream before returning.
+ *
+ * Errors: every call returns a tq_status. Argument errors leave the state
+ * unchanged. After a CUDA error the state is poisoned and every later call
+ * on it returns TQ_ERR_STATE; only tq_free is then valid.
+ */
+#ifndef TANQ_H
+#define TANQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tq_state tq_state; /* opaque; owns the device copy of vec(rho) */
+
+typedef enum {
+  TQ_FP64 = 0,  /* rho complex128, superoperator products in FP64 */
+  TQ_SPLIT = 1  /* rho complex64, products in FP32 (FP64 superoperator build,
+                   fusion, trace renormalisation and readouts) */
+} tq_precision;
+
+typedef enum {
+  TQ_OK = 0,
+  TQ_ERR_ARG = 1,         /* bad size, null pointer, unknown kind/name, bad parameter */
+  TQ_ERR_QUBIT = 2,       /* qubit index out of range or repeated */
+  TQ_ERR_OOM = 3,         /* device or pinned host allocation failed */
+  TQ_ERR_CUDA = 4,        /* a CUDA call failed; the state is now poisoned */
+  TQ_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+  TQ_ERR_STATE = 6,       /* the state was poisoned by an earlier CUDA error */
+  TQ_ERR_UNSUPPORTED = 7  /* valid request this build does not provide */
+} tq_status;
+
+/* Named gates (textbook definitions; Sec. 4 Table 2 lists the gate family).
+ * Parameters: RX/RY/RZ/RZZ take params[0] = angle theta with
+ * RX = exp(-i theta X/2), RY = exp(-i theta Y/2), RZ = diag(e^{-i theta/2},
+ * e^{i theta/2}), RZZ = exp(-i theta Z(x)Z/2). SU2 takes params[0..3] = four
+ * real numbers (not all zero) normalised to a unit quaternion (a, b, c, d):
+ * U = [[a+ib, c+id], [-c+id, a-ib]]; four i.i.d. normal draws give a
+ * Haar-random SU(2). CX/CZ: qubits[0] is the control, qubits[1] the target. */
+typedef enum {
+  TQ_GATE_ID = 0, TQ_GATE_H, TQ_GATE_X, TQ_GATE_Y, TQ_GATE_Z, TQ_GATE_S,
+  TQ_GATE_SDG, TQ_GATE_T, TQ_GATE_TDG, TQ_GATE_SX, TQ_GATE_RX, TQ_GATE_RY,
+  TQ_GATE_RZ, TQ_GATE_SU2,
+  TQ_GATE_CX = 32, TQ_GATE_CZ, TQ_GATE_SWAP, TQ_GATE_RZZ
+} tq_gate;
+
+/* Named noise channels (Sec. 3.5). k is the number of qubits the op lists.
+ *  DEPOLARIZING  params[0] = p in [0, 4^k/(4^k-1)]: rho -> (1-p) rho +
+ *                p (I/2^k) (x) Tr_Q(rho), given as the 4^k Pauli Kraus
+ *                operators sqrt(1 - p (4^k-1)/4^k) I and sqrt(p/4^k) P;
+ *                k in 1..2.
+ *  AMPLITUDE_DAMPING params[0] = gamma in [0,1]: K0 = [[1,0],[0,sqrt(1-g)]],
+ *                K1 = [[0,sqrt(g)],[0,0]]; k = 1.
+ *  PHASE_DAMPING params[0] = lambda in [0,1]: K0 = [[1,0],[0,sqrt(1-l)]],
+ *                K1 = [[0,0],[0,sqrt(l)]]; k = 1.
+ *  THERMAL       params = (t, T1, T2), t >= 0, T1 > 0, 0 < T2 <= 2 T1:
+ *                zero-temperature relaxation rho00 += (1-e^{-t/T1}) rho11,
+ *                rho11 *= e^{-t/T1}, rho01 *= e^{-t/T2}; applied
+ *                independently to each of the k (1..2) listed qubits. */
+typedef enum {
+  TQ_CH_DEPOLARIZING = 0,
+  TQ_CH_AMPLITUDE_DAMPING = 1,
+  TQ_CH_PHASE_DAMPING = 2,
+  TQ_CH_THERMAL = 3
+} tq_channel;
+
+typedef enum {
+  TQ_OP_UNITARY = 0,  /* mats = one 2^k x 2^k matrix U: rho -> U rho U^dag (Eq. 1) */
+  TQ_OP_KRAUS = 1,    /* mats = m matrices K_i: rho -> sum_i K_i rho K_i^dag; K need
+                         not be trace preserving (Sec. 2.1: G need not be unitary) */
+  TQ_OP_GATE = 2,     /* name = tq_gate, params as documented there */
+  TQ_OP_CHANNEL = 3   /* name = tq_channel, params as documented there */
+} tq_op_kind;
+
+/* One circuit op. For UNITARY/KRAUS, mats points to m (1 for UNITARY)
+ * matrices in the layout above; for GATE/CHANNEL it is ignored. */
+typedef struct tq_op {
+  int32_t kind;        /* tq_op_kind */
+  int32_t k;           /* number of qubits, 1..4 */
+  int32_t qubits[4];   /* qubits[0..k-1], distinct, each in [0, n) */
+  int32_t m;           /* number of Kraus matrices (KRAUS), else ignored */
+  int32_t name;        /* tq_gate (GATE) or tq_channel (CHANNEL) */
+  double params[4];
+  const double* mats;
+} tq_op;
+
+/* ---- states ----------------------------------------------------------- */
+
+/* Create rho = |0..0><0..0| for n qubits (1 <= n <= 16; device memory
+ * 16 * 4^n bytes in TQ_FP64, 8 * 4^n in TQ_SPLIT), working on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream) of the current device. */
+tq_status tq_create(int n_qubits, int precision, void* cuda_stream, tq_state** out);
+
+/* As tq_create, but vec(rho) lives in caller-owned device memory `rho_dev`
+ * of `bytes` bytes (>= 16*4^n FP64 / 8*4^n SPLIT, 256-byte aligned), for
+ * example a tensor from PyTorch's caching allocator. The buffer is
+ * initialised to |0..0><0..0| and must outlive the state. */
+tq_status tq_create_on(int n_qubits, int precision, void* cuda_stream, void* rho_dev,
+                       size_t bytes, tq_state** out);
+
+void tq_free(tq_state* s);
+
+/* Number of qubits and precision of a state (TQ_ERR_ARG on NULL). */
+tq_status tq_info(const tq_state* s, int* n_qubits, int* precision);
+
+/* Reset rho to |0..0><0..0| (asynchronous). */
+tq_status tq_reset(tq_state* s);
+
+/* Device address of vec(rho) (complex128 or complex64, interleaved), for
+ * zero-copy interop on the state's stream. */
+tq_status tq_rho_device_ptr(tq_state* s, void** out);
+
+/* Copy vec(rho) out to / in from host memory: 2 * 4^n doubles, interleaved
+ * (re, im) in vec order (index r + c 2^n). Split states convert from/to
+ * complex64. tq_get_rho waits for the stream. */
+tq_status tq_get_rho(tq_state* s, double* out);
+tq_status tq_set_rho(tq_state* s, const double* in);
+
+/* ---- evolution -------------------------------------------------------- */
+
+/* rho -> U rho U^dag with U a 2^k x 2^k matrix on qubits[0..k-1], 1 <= k <= 4
+ * (Eq. 1; applied as vec(rho) -> (conj(U) (x) U) vec(rho), Sec. 3.1). */
+tq_status tq_apply_gate(tq_state* s, const int* qubits, int k, const double* U);
+
+/* rho -> sum_{i<m} K_i rho K_i^dag, K_i 2^k x 2^k on qubits[0..k-1]
+ * (Sec. 3.1 Kraus sum; superoperator S = sum_i conj(K_i) (x) K_i). */
+tq_status tq_apply_kraus(tq_state* s, const int* qubits, int k, int m, const double* K);
+
+/* Run ops[0..n_ops-1] in order (Eq. 2). Ops are fused into blocks of at most
+ * max_fuse_width qubits (1..4) by merging each op into the latest block that
+ * shares a qubit with it when the union stays within the width and no
+ * later block touches those qubits (Sec. 3.3, generalised); 0 applies every
+ * op as its own pass (no fusion); -1 lets the library's cost model choose
+ * the width for this n and precision. Superoperators are built and fused in
+ * FP64 on the GPU. Asynchronous. If n_blocks_out is not NULL it receives the
+ * number of fused blocks applied. */
+tq_status tq_run_circuit(tq_state* s, const tq_op* ops, size_t n_ops, int max_fuse_width,
+                         size_t* n_blocks_out);
+
+/* ---- readouts (FP64 reductions over the diagonal, Sec. 2.1) ------------ */
+
+/* Tr(rho) = sum_x rho[x][x]. */
+tq_status tq_trace(tq_state* s, double* re, double* im);
+
+/* out[i] = Re Tr(rho Z_{masks[i]}) for i < n_masks (Z on every qubit whose
+ * bit is set in the mask; mask 0 gives Re Tr rho). In TQ_SPLIT the values
+ * are divided by Re Tr(rho) (trace renormalisation). */
+tq_status tq_expect_z(tq_state* s, const uint64_t* masks, int n_masks, double* out);
+
+/* out[x] = Re rho[x][x] for x < 2^n: the probabilities of measuring every
+ * qubit in the computational basis (renormalised to sum 1 in TQ_SPLIT). */
+tq_status tq_probs(tq_state* s, double* out);
+
+/* ---- host-side helpers (no GPU work; usable without a device) ----------- */
+
+/* Matrix of a named gate: *k_out = 1 or 2, U_out receives 2^k x 2^k complex
+ * (room for 16 complex = 32 doubles is enough). */
+tq_status tq_gate_matrix(int gate, const double* params, int* k_out, double* U_out);
+
+/* Kraus set of a named channel on k qubits: *m_out matrices of 2^k x 2^k
+ * written to K_out, which has room for `capacity` matrices. With K_out NULL
+ * only *m_out is set (count query); TQ_ERR_ARG if capacity is too small
+ * (*m_out still tells the count needed). */
+tq_status tq_channel_kraus(int channel, int k, const double* params, int capacity,
+                           int* m_out, double* K_out);
+
+/* Fusion plan only (the same planner tq_run_circuit uses): block_of_op[i]
+ * receives the index of the block op i joins, block_width[b] the number of
+ * qubits of block b (arrays of n_ops entries); *n_blocks_out the count. */
+tq_status tq_plan_fusion(int n_qubits, const tq_op* ops, size_t n_ops, int max_fuse_width,
+                         int precision, int* block_of_op, int* block_width,
+                         size_t* n_blocks_out);
+
+/* Base vec index of group g for a block whose 2k target bit positions are
+ * positions[0..2k-1] (any order): g with a zero bit inserted at every target
+ * position, in increasing position order. For k = 1 and positions (q, q+n)
+ * this is the index s_i of Sec. 3.1. */
+uint64_t tq_group_base(uint64_t g, const int* positions, int n_positions);
+
+const char* tq_status_string(int status);
+
+/* Library version string. */
+const char* tq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TANQ_H */

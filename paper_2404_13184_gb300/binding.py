@@ -1,0 +1,283 @@
+"""Thin Python binding of the C ABI in ``include/tanq.h`` (ctypes).
+
+Argument marshalling only: op names become the header's enum values, numpy
+arrays become pointers, vec(rho) is reshaped to and from the matrix rho[r, c]
+(vec index r + c 2^n). Every step of the simulation runs in the CUDA
+library; there is no CPU fallback, and loading fails loudly when
+``libtanq.so`` has not been built.
+
+PyTorch supplies the plumbing when it is importable: the state's CUDA stream
+is the current torch stream and vec(rho) is a tensor from torch's caching
+allocator (``tq_create_on``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtanq.so")
+
+# enum values of include/tanq.h (a CPU test checks them against the header)
+PRECISION = {"fp64": 0, "split": 1}
+STATUS = {0: "TQ_OK", 1: "TQ_ERR_ARG", 2: "TQ_ERR_QUBIT", 3: "TQ_ERR_OOM", 4: "TQ_ERR_CUDA",
+          5: "TQ_ERR_TIMEOUT", 6: "TQ_ERR_STATE", 7: "TQ_ERR_UNSUPPORTED"}
+GATES = {"id": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,
+         "rx": 10, "ry": 11, "rz": 12, "su2": 13, "cx": 32, "cz": 33, "swap": 34, "rzz": 35}
+CHANNELS = {"depol": 0, "ad": 1, "pd": 2, "thermal": 3}
+OP_UNITARY, OP_KRAUS, OP_GATE, OP_CHANNEL = 0, 1, 2, 3
+
+
+class TqOp(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("k", c_int32), ("qubits", c_int32 * 4), ("m", c_int32),
+                ("name", c_int32), ("params", c_double * 4), ("mats", POINTER(c_double))]
+
+
+class TqError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({_lib.tq_status_string(status).decode() if _lib else ''})")
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function
+_SIGNATURES = [
+    ("tq_create", c_int, [c_int, c_int, c_void_p, POINTER(c_void_p)]),
+    ("tq_create_on", c_int, [c_int, c_int, c_void_p, c_void_p, c_size_t, POINTER(c_void_p)]),
+    ("tq_free", None, [c_void_p]),
+    ("tq_info", c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    ("tq_reset", c_int, [c_void_p]),
+    ("tq_rho_device_ptr", c_int, [c_void_p, POINTER(c_void_p)]),
+    ("tq_get_rho", c_int, [c_void_p, POINTER(c_double)]),
+    ("tq_set_rho", c_int, [c_void_p, POINTER(c_double)]),
+    ("tq_apply_gate", c_int, [c_void_p, POINTER(c_int), c_int, POINTER(c_double)]),
+    ("tq_apply_kraus", c_int, [c_void_p, POINTER(c_int), c_int, c_int, POINTER(c_double)]),
+    ("tq_run_circuit", c_int, [c_void_p, POINTER(TqOp), c_size_t, c_int, POINTER(c_size_t)]),
+    ("tq_trace", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
+    ("tq_expect_z", c_int, [c_void_p, POINTER(c_uint64), c_int, POINTER(c_double)]),
+    ("tq_probs", c_int, [c_void_p, POINTER(c_double)]),
+    ("tq_gate_matrix", c_int, [c_int, POINTER(c_double), POINTER(c_int), POINTER(c_double)]),
+    ("tq_channel_kraus", c_int, [c_int, c_int, POINTER(c_double), c_int, POINTER(c_int), POINTER(c_double)]),
+    ("tq_plan_fusion", c_int, [c_int, POINTER(TqOp), c_size_t, c_int, c_int, POINTER(c_int), POINTER(c_int),
+                               POINTER(c_size_t)]),
+    ("tq_group_base", c_uint64, [c_uint64, POINTER(c_int), c_int]),
+    ("tq_status_string", ctypes.c_char_p, [c_int]),
+    ("tq_version", ctypes.c_char_p, []),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load libtanq.so (raises if it is missing: build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_2404_13184_gb300.build.build() (or "
+                           "__graft_entry__.build()) first; there is no fallback path")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise TqError(st, what)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _mats_array(mats) -> np.ndarray:
+    arr = np.ascontiguousarray(np.stack([np.asarray(m, dtype=np.complex128) for m in mats]))
+    return arr.view(np.float64).reshape(-1)
+
+
+class Program:
+    """Ops marshalled into a tq_op array (kept alive with their matrices)."""
+
+    def __init__(self, ops):
+        self.n_ops = len(ops)
+        self.arr = (TqOp * max(1, len(ops)))()
+        self._keep = []
+        for i, (name, qubits, params) in enumerate(ops):
+            o = self.arr[i]
+            o.k = len(qubits)
+            for j, q in enumerate(qubits):
+                o.qubits[j] = int(q)
+            if name in GATES:
+                o.kind, o.name = OP_GATE, GATES[name]
+                for j, v in enumerate(params):
+                    o.params[j] = float(v)
+            elif name in CHANNELS:
+                o.kind, o.name = OP_CHANNEL, CHANNELS[name]
+                for j, v in enumerate(params):
+                    o.params[j] = float(v)
+            elif name in ("unitary", "kraus"):
+                m = _mats_array(params)
+                self._keep.append(m)
+                o.kind = OP_UNITARY if name == "unitary" else OP_KRAUS
+                o.m = len(params)
+                o.mats = _dptr(m)
+            else:
+                raise ValueError(f"unknown op {name!r}")
+
+
+def plan_fusion(n: int, ops, width: int, precision: str = "fp64"):
+    """(block index of every op, width of every block) from the library's planner."""
+    lib = load()
+    prog = ops if isinstance(ops, Program) else Program(ops)
+    boo = (c_int * max(1, prog.n_ops))()
+    bw = (c_int * max(1, prog.n_ops))()
+    nb = c_size_t(0)
+    _check(lib.tq_plan_fusion(n, prog.arr, prog.n_ops, width, PRECISION[precision], boo, bw, ctypes.byref(nb)),
+           "tq_plan_fusion")
+    return list(boo[:prog.n_ops]), list(bw[:nb.value])
+
+
+def gate_matrix(name: str, params=()) -> np.ndarray:
+    lib = load()
+    p = np.zeros(4)
+    p[:len(params)] = params
+    out = np.zeros(32)
+    k = c_int(0)
+    _check(lib.tq_gate_matrix(GATES[name], _dptr(p), ctypes.byref(k), _dptr(out)), "tq_gate_matrix")
+    d = 1 << k.value
+    return out[:2 * d * d].view(np.complex128).reshape(d, d)
+
+
+def channel_kraus(name: str, k: int, params) -> list[np.ndarray]:
+    lib = load()
+    p = np.zeros(4)
+    p[:len(params)] = params
+    m = c_int(0)
+    _check(lib.tq_channel_kraus(CHANNELS[name], k, _dptr(p), 0, ctypes.byref(m), None), "tq_channel_kraus")
+    d = 1 << k
+    out = np.zeros(m.value * 2 * d * d)
+    _check(lib.tq_channel_kraus(CHANNELS[name], k, _dptr(p), m.value, ctypes.byref(m), _dptr(out)), "tq_channel_kraus")
+    arr = out.view(np.complex128).reshape(m.value, d, d)
+    return [arr[i] for i in range(m.value)]
+
+
+def group_base(g: int, positions) -> int:
+    lib = load()
+    pos = (c_int * len(positions))(*positions)
+    return int(lib.tq_group_base(g, pos, len(positions)))
+
+
+def _torch_plumbing():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch
+    except Exception:
+        pass
+    return None
+
+
+class State:
+    """A density matrix on the GPU (tq_state)."""
+
+    def __init__(self, n: int, precision: str = "fp64", stream=None, torch_memory: bool = True):
+        lib = load()
+        self.n = n
+        self.precision = precision
+        self._buf = None
+        self._h = c_void_p()
+        torch = _torch_plumbing()
+        if stream is None and torch is not None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        prec = PRECISION[precision]
+        if torch_memory and torch is not None:
+            nbytes = (16 if precision == "fp64" else 8) << (2 * n)
+            self._buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            _check(lib.tq_create_on(n, prec, c_void_p(stream), c_void_p(self._buf.data_ptr()), nbytes,
+                                    ctypes.byref(self._h)), "tq_create_on")
+        else:
+            _check(lib.tq_create(n, prec, c_void_p(stream), ctypes.byref(self._h)), "tq_create")
+
+    # -- lifetime
+    def free(self):
+        if self._h:
+            _lib.tq_free(self._h)
+            self._h = c_void_p()
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    # -- evolution
+    def run(self, ops, width: int = -1) -> int:
+        prog = ops if isinstance(ops, Program) else Program(ops)
+        nb = c_size_t(0)
+        _check(_lib.tq_run_circuit(self._h, prog.arr, prog.n_ops, width, ctypes.byref(nb)), "tq_run_circuit")
+        return nb.value
+
+    def apply_gate(self, qubits, U):
+        q = (c_int * len(qubits))(*qubits)
+        m = _mats_array([U])
+        _check(_lib.tq_apply_gate(self._h, q, len(qubits), _dptr(m)), "tq_apply_gate")
+
+    def apply_kraus(self, qubits, kraus):
+        q = (c_int * len(qubits))(*qubits)
+        m = _mats_array(kraus)
+        _check(_lib.tq_apply_kraus(self._h, q, len(qubits), len(kraus), _dptr(m)), "tq_apply_kraus")
+
+    def reset(self):
+        _check(_lib.tq_reset(self._h), "tq_reset")
+
+    # -- readouts
+    def trace(self) -> complex:
+        re, im = c_double(), c_double()
+        _check(_lib.tq_trace(self._h, ctypes.byref(re), ctypes.byref(im)), "tq_trace")
+        return complex(re.value, im.value)
+
+    def expect_z(self, masks) -> np.ndarray:
+        masks = [int(m) for m in masks]
+        arr = (c_uint64 * max(1, len(masks)))(*masks)
+        out = np.zeros(max(1, len(masks)))
+        _check(_lib.tq_expect_z(self._h, arr, len(masks), _dptr(out)), "tq_expect_z")
+        return out[:len(masks)]
+
+    def probs(self) -> np.ndarray:
+        out = np.zeros(1 << self.n)
+        _check(_lib.tq_probs(self._h, _dptr(out)), "tq_probs")
+        return out
+
+    def vec(self) -> np.ndarray:
+        out = np.zeros(2 << (2 * self.n))
+        _check(_lib.tq_get_rho(self._h, _dptr(out)), "tq_get_rho")
+        return out.view(np.complex128)
+
+    def rho(self) -> np.ndarray:
+        """rho[r, c] from vec(rho) (column-stacked: vec index r + c 2^n)."""
+        N = 1 << self.n
+        return self.vec().reshape(N, N).T.copy()
+
+    def set_rho(self, rho: np.ndarray):
+        N = 1 << self.n
+        v = np.ascontiguousarray(np.asarray(rho, dtype=np.complex128).T).reshape(N * N)
+        flat = v.view(np.float64)
+        _check(_lib.tq_set_rho(self._h, _dptr(flat)), "tq_set_rho")
+
+    def device_ptr(self) -> int:
+        p = c_void_p()
+        _check(_lib.tq_rho_device_ptr(self._h, ctypes.byref(p)), "tq_rho_device_ptr")
+        return p.value

@@ -1,0 +1,222 @@
+// Apply kernels: one pass of a fused width-K superoperator over vec(rho)
+// (TANQ-Sim Sec. 3.1, the C1/C2 update generalised to K <= 4).
+//
+// vec(rho) has 4^n entries; a width-K block on qubits q_0..q_{K-1} splits the
+// 2n index bits into 2K target bits (q_j and q_j + n) and 2n - 2K group bits.
+// Group g's base index is g with zeros inserted at the target bits; its 4^K
+// entries sit at base + off[l], where bit j of l selects row bit q_j and bit
+// K + j selects column bit q_j + n. Each group is replaced by S x (x = its
+// 4^K entries). Groups are disjoint, so the update runs in place: every
+// entry is read once and written once, by the CTA that owns its group.
+#include <algorithm>
+#include <mutex>
+
+#include "tq_device.cuh"
+
+namespace tq {
+
+namespace {
+
+template <typename T2>
+struct CplxOps;
+
+template <>
+struct CplxOps<double2> {
+  __device__ __forceinline__ static double2 zero() { return make_double2(0.0, 0.0); }
+  // Shared-memory load kept inside the loop (volatile): S stays in shared
+  // memory instead of being hoisted into (and spilled from) registers.
+  __device__ __forceinline__ static double2 lds(const double2* p) {
+    double2 v;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];"
+                 : "=d"(v.x), "=d"(v.y)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+  }
+  __device__ __forceinline__ static void fma(double2& acc, double2 a, double2 b) {
+    acc.x = ::fma(a.x, b.x, acc.x);
+    acc.x = ::fma(-a.y, b.y, acc.x);
+    acc.y = ::fma(a.x, b.y, acc.y);
+    acc.y = ::fma(a.y, b.x, acc.y);
+  }
+};
+
+template <>
+struct CplxOps<float2> {
+  __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static float2 lds(const float2* p) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+  }
+  __device__ __forceinline__ static void fma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+  }
+};
+
+// Widths 1 and 2: one thread per group, the group's 4^K entries in
+// registers. S (16 or 256 complex) is staged in shared memory; for width 1
+// the compiler keeps it in registers across the group loop, for width 2 it is
+// re-read from shared memory (warp-uniform broadcast) for every group.
+// Grid-stride over groups; consecutive threads take consecutive groups, so a
+// warp's loads of one local index are contiguous whenever the low index bits
+// are group bits.
+template <typename T2, int K>
+__global__ void __launch_bounds__(256) k_apply_direct(T2* rho, const T2* __restrict__ S,
+                                                      const __grid_constant__ ApplyParams p) {
+  constexpr int D = 1 << (2 * K);
+  __shared__ T2 sS[D * D];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sS[i] = S[i];
+  __syncthreads();
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < p.n_groups;
+       g += stride) {
+    unsigned long long base = g;
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) {
+      const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
+      base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
+    }
+    T2 x[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) x[l] = rho[base + p.off[l]];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      T2 acc = CplxOps<T2>::zero();
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+        CplxOps<T2>::fma(acc, K == 1 ? sS[i * D + j] : CplxOps<T2>::lds(&sS[i * D + j]), x[j]);
+      rho[base + p.off[i]] = acc;
+    }
+  }
+}
+
+// Widths 3 and 4: a CTA stages the entries of G consecutive groups (4^K x G)
+// in shared memory, then thread (rowset, gi) computes rows i = rowset +
+// (256/G) r of group gi and writes them straight back to global memory (the
+// tile's entries were all read before the first write). S sits in shared
+// memory when it fits (K = 3) and is read through L1/L2 otherwise (K = 4).
+template <typename T2, int K, int G, bool S_SMEM>
+__global__ void __launch_bounds__(256) k_apply_tiled(T2* rho, const T2* __restrict__ S,
+                                                     const __grid_constant__ ApplyParams p) {
+  constexpr int D = 1 << (2 * K);
+  constexpr int ROWSETS = 256 / G;
+  constexpr int ROWS = D / ROWSETS;  // rows per thread
+  constexpr int CH = 8;              // rows per accumulation chunk
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* sOff = reinterpret_cast<unsigned long long*>(smem_raw);
+  T2* sX = reinterpret_cast<T2*>(sOff + D);
+  T2* sS = sX + D * G;
+  for (int l = threadIdx.x; l < D; l += blockDim.x) {
+    unsigned long long v = 0;
+    for (int j = 0; j < K; ++j) {
+      if ((l >> j) & 1) v |= 1ull << p.q[j];
+      if ((l >> (K + j)) & 1) v |= 1ull << (p.q[j] + p.n);
+    }
+    sOff[l] = v;
+  }
+  if (S_SMEM)
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) sS[e] = S[e];
+  __syncthreads();
+  const int gi = threadIdx.x % G;
+  const int rowset = threadIdx.x / G;
+  const unsigned long long n_tiles = (p.n_groups + G - 1) / G;
+  for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const unsigned long long g0 = tile * G;
+    for (int e = threadIdx.x; e < D * G; e += blockDim.x) {
+      const int l = e / G, gg = e % G;
+      const unsigned long long g = g0 + gg;
+      if (g < p.n_groups) sX[e] = rho[deposit_zeros(g, p.pos, 2 * K) + sOff[l]];
+    }
+    __syncthreads();
+    const unsigned long long g = g0 + gi;
+    if (g < p.n_groups) {
+      const unsigned long long base = deposit_zeros(g, p.pos, 2 * K);
+#pragma unroll 1
+      for (int r0 = 0; r0 < ROWS; r0 += CH) {
+        T2 acc[CH];
+#pragma unroll
+        for (int r = 0; r < CH; ++r) acc[r] = CplxOps<T2>::zero();
+#pragma unroll 4
+        for (int j = 0; j < D; ++j) {
+          const T2 xj = sX[j * G + gi];
+#pragma unroll
+          for (int r = 0; r < CH; ++r) {
+            const int i = rowset + ROWSETS * (r0 + r);
+            const T2 s = S_SMEM ? sS[i * D + j] : __ldg(&S[i * D + j]);
+            CplxOps<T2>::fma(acc[r], s, xj);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < CH; ++r) {
+          const int i = rowset + ROWSETS * (r0 + r);
+          rho[base + sOff[i]] = acc[r];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T2, int K, int G, bool S_SMEM>
+size_t tiled_smem_bytes() {
+  constexpr int D = 1 << (2 * K);
+  return D * sizeof(unsigned long long) + (size_t)D * G * sizeof(T2) + (S_SMEM ? (size_t)D * D * sizeof(T2) : 0);
+}
+
+template <typename T2, int K, int G, bool S_SMEM>
+cudaError_t run_tiled(T2* rho, const T2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
+  static std::once_flag once;
+  static int per_sm = 1;
+  const size_t smem = tiled_smem_bytes<T2, K, G, S_SMEM>();
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(k_apply_tiled<T2, K, G, S_SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apply_tiled<T2, K, G, S_SMEM>, 256, smem) == cudaSuccess && b > 0)
+      per_sm = b;
+  });
+  const unsigned long long n_tiles = (p.n_groups + G - 1) / G;
+  const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_tiles, (unsigned long long)num_sms * per_sm));
+  k_apply_tiled<T2, K, G, S_SMEM><<<grid, 256, smem, st>>>(rho, S, p);
+  return cudaGetLastError();
+}
+
+template <typename T2, int K>
+cudaError_t run_direct(T2* rho, const T2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
+  const unsigned long long blocks = (p.n_groups + 255) / 256;
+  const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(blocks, (unsigned long long)num_sms * 8));
+  k_apply_direct<T2, K><<<grid, 256, 0, st>>>(rho, S, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyParams& p, int num_sms,
+                         cudaStream_t st) {
+  if (precision == 0) {
+    double2* r = static_cast<double2*>(rho);
+    const double2* s = static_cast<const double2*>(S);
+    switch (p.width) {
+      case 1: return run_direct<double2, 1>(r, s, p, num_sms, st);
+      case 2: return run_direct<double2, 2>(r, s, p, num_sms, st);
+      case 3: return run_tiled<double2, 3, 32, true>(r, s, p, num_sms, st);
+      case 4: return run_tiled<double2, 4, 16, false>(r, s, p, num_sms, st);
+    }
+  } else {
+    float2* r = static_cast<float2*>(rho);
+    const float2* s = static_cast<const float2*>(S);
+    switch (p.width) {
+      case 1: return run_direct<float2, 1>(r, s, p, num_sms, st);
+      case 2: return run_direct<float2, 2>(r, s, p, num_sms, st);
+      case 3: return run_tiled<float2, 3, 32, true>(r, s, p, num_sms, st);
+      case 4: return run_tiled<float2, 4, 32, false>(r, s, p, num_sms, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tq

@@ -1,0 +1,92 @@
+// Device-side types and kernel entry points shared by the library's CUDA
+// translation units (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace tq {
+
+// One op after resolution: k qubits, m Kraus matrices at kraus_off (complex
+// units) in the uploaded Kraus blob, its superoperator at sop_off.
+struct OpDesc {
+  int k;
+  int m;
+  long long kraus_off;
+  long long sop_off;
+};
+
+// One fused block: `width` qubits, members [member_off, member_off +
+// n_members) in the member table, fused superoperator at sb_off (complex
+// units; D x D row-major with D = 4^width).
+struct BlockDesc {
+  int width;
+  int n_members;
+  int member_off;
+  int pad;
+  long long sb_off;
+};
+
+// A member op of a block: which op, and the block-local position of each of
+// its qubits (op local bit j sits at block local bit pos[j]).
+struct MemberDesc {
+  int op;
+  int k;
+  int pos[4];
+};
+
+// Work item of the fusion kernel: block index and first column.
+struct FuseWork {
+  int block;
+  int col0;
+};
+
+// Launch parameters of one apply pass of a width-K block over vec(rho).
+// pos: the 2K target bit positions, ascending (for the group-base deposit).
+// off: vec offset of every local index l < 4^K (direct kernels, K <= 2).
+// q:   block qubits in local order (row bits; column bits are q + n).
+struct ApplyParams {
+  unsigned long long n_groups;
+  int n;
+  int width;
+  int npos;
+  int pos[8];
+  int q[4];
+  unsigned long long off[16];
+};
+
+// Insert a zero bit at each of the first `npos` positions of `pos`
+// (ascending): the base index of group g (Sec. 3.1, index s_i, generalised).
+__host__ __device__ __forceinline__ unsigned long long deposit_zeros(unsigned long long g,
+                                                                    const int* pos, int npos) {
+  for (int i = 0; i < npos; ++i) {
+    const unsigned long long low = g & ((1ull << pos[i]) - 1ull);
+    g = ((g >> pos[i]) << (pos[i] + 1)) | low;
+  }
+  return g;
+}
+
+// --- kernel launchers (tq_kernels.cu) -------------------------------------
+cudaError_t launch_build_superops(const double2* kraus, const OpDesc* ops, int n_ops,
+                                  int max_dim2, double2* sops, cudaStream_t st);
+cudaError_t launch_fuse(const double2* sops, const OpDesc* ops, const BlockDesc* blocks,
+                        const MemberDesc* members, const FuseWork* work, int n_work,
+                        double2* sb64, float2* sb32, cudaStream_t st);
+cudaError_t launch_init_zero_state(void* rho, int n, int precision, cudaStream_t st);
+// Reductions over the diagonal: quantities [Re tr, Im tr, Re Tr(rho Z_mask_i)...]
+// partials: gridDim x nq doubles of scratch; out: nq doubles (device).
+int diag_reduce_grid(int n);
+cudaError_t launch_diag_reduce(const void* rho, int n, int precision, const unsigned long long* masks,
+                               int n_masks, double* partials, double* out, bool normalize, cudaStream_t st);
+cudaError_t launch_diag_probs(const void* rho, int n, int precision, const double* trace_or_null,
+                              double* out, cudaStream_t st);
+cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t count, cudaStream_t st);
+cudaError_t launch_convert_f32_to_f64(const float* in, double* out, size_t count, cudaStream_t st);
+
+// --- apply kernels (tq_apply.cu) ------------------------------------------
+// One pass of a fused block over vec(rho). S: 4^K x 4^K superoperator,
+// row-major (double2 for FP64 states, float2 for split states).
+cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyParams& p,
+                         int num_sms, cudaStream_t st);
+
+}  // namespace tq

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+FP64 states must match within 1e-12 max-abs (entries, trace, <Z> values).
+Split states (complex64 storage, FP32 products) are checked against the
+bound stated for them: 2e-6 max-abs per entry after one op on a unit-trace
+state, and the per-result bounds of the circuit tests below."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dm_oracle as O
+from paper_2404_13184_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+def random_general_matrix(n, seed):
+    """A unit-trace Hermitian state plus a non-Hermitian part, so that a
+    missing conjugate or a transposed operand shows up."""
+    rho = W.random_density_matrix(n, seed)
+    rng = np.random.default_rng(seed + 1)
+    N = 1 << n
+    return rho + 0.2 * (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))) / N
+
+
+def maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))))
+
+
+QUBIT_CASES = {
+    1: [(0,)],
+    2: [(0,), (1,), (0, 1), (1, 0)],
+    3: [(0,), (2,), (2, 0), (1, 2), (0, 1, 2), (2, 0, 1)],
+    5: [(0,), (4,), (1, 3), (4, 0), (0, 2, 4), (3, 1, 0), (0, 1, 2, 3), (4, 2, 0, 1)],
+    7: [(0,), (3,), (6,), (0, 1), (6, 5), (2, 6), (0, 1, 2), (6, 3, 0), (0, 1, 2, 3), (6, 0, 4, 2)],
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("n", sorted(QUBIT_CASES))
+def test_single_kraus_op_every_position(tq, n, precision):
+    rho = random_general_matrix(n, 100 + n)
+    for ci, qubits in enumerate(QUBIT_CASES[n]):
+        k = len(qubits)
+        Ks = W.random_kraus(k, 2, 1000 * n + ci)
+        want = O.apply_kraus(rho, Ks, list(qubits))
+        with tq.State(n, precision) as st:
+            st.set_rho(rho)
+            st.apply_kraus(list(qubits), Ks)
+            got = st.rho()
+        tol = TOL64 if precision == "fp64" else 2e-6
+        assert maxabs(got, want) < tol, (qubits, maxabs(got, want))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_unitary_ops(tq, precision):
+    n = 6
+    rho = random_general_matrix(n, 7)
+    rng = np.random.default_rng(3)
+    for k in (1, 2, 3, 4):
+        a = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+        U, _ = np.linalg.qr(a)
+        qubits = [int(v) for v in rng.choice(n, size=k, replace=False)]
+        want = O.apply_kraus(rho, [U], qubits)
+        with tq.State(n, precision) as st:
+            st.set_rho(rho)
+            st.apply_gate(qubits, U)
+            got = st.rho()
+        assert maxabs(got, want) < (TOL64 if precision == "fp64" else 2e-6), (k, qubits)
+
+
+def test_plain_6q_unfused_matches_oracle(tq):
+    c = W.plain_6q()
+    want = O.run_circuit(c.n, c.ops)
+    with tq.State(c.n, "fp64") as st:
+        nb = st.run(c.ops, width=0)
+        assert nb == len(c.ops)
+        got = st.rho()
+        tr = st.trace()
+        zs = st.expect_z([1 << q for q in range(c.n)])
+    assert maxabs(got, want) < TOL64
+    assert abs(tr - O.trace(want)) < TOL64
+    for q in range(c.n):
+        assert abs(zs[q] - O.expect_z(want, 1 << q)) < TOL64
+
+
+@pytest.mark.parametrize("width", [0, 1, 2, 3, 4, -1])
+@pytest.mark.parametrize("n", [4, 5, 8])
+def test_fused_circuits_match_oracle_fp64(tq, n, width):
+    c = W.random_noisy_circuit(n, 60, 40 + n, gate_set=("h", "s", "rz", "cx", "su2", "rzz"))
+    c.ops += [("thermal", [0, n - 1], (300e-9, 100e-6, 80e-6)), ("pd", [n // 2], (0.05,))]
+    want = O.run_circuit(n, c.ops)
+    with tq.State(n, "fp64") as st:
+        st.run(c.ops, width=width)
+        got = st.rho()
+    assert maxabs(got, want) < TOL64
+
+
+@pytest.mark.parametrize("width", [0, 2, 3, 4])
+def test_fused_circuits_split_bound(tq, width):
+    n = 7
+    c = W.random_noisy_circuit(n, 120, 77, gate_set=("h", "rx", "rz", "cx", "su2"))
+    want = O.run_circuit(n, c.ops)
+    with tq.State(n, "split") as st:
+        st.run(c.ops, width=width)
+        got = st.rho()
+        zs = st.expect_z([1 << q for q in range(n)] + [3, 0b1010101])
+    assert maxabs(got, want) < 2e-6
+    wz = [O.expect_z(want, m) for m in [1 << q for q in range(n)] + [3, 0b1010101]]
+    assert maxabs(zs, wz) < 1e-5
+
+
+@pytest.mark.parametrize("width", [0, 1, 2, 3, 4])
+def test_layered_thermal_widths_match_oracle(tq, width):
+    # the 12-qubit layered thermal workload's structure at 8 qubits and 200 gates
+    c = W.layered_thermal(n=8, n_gates=200)
+    want = O.run_circuit(c.n, c.ops)
+    with tq.State(c.n, "fp64") as st:
+        st.run(c.ops, width=width)
+        got = st.rho()
+    assert maxabs(got, want) < TOL64
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("split", 2e-5)])
+def test_tfim_8q_zz_per_step(tq, precision, tol):
+    c = W.tfim_ring(n=8, steps=30)
+    rho = O.zero_state(c.n)
+    with tq.State(c.n, precision) as st:
+        worst = 0.0
+        for (s0, s1) in c.steps:
+            step_ops = c.ops[s0:s1]
+            rho = O.run_circuit(c.n, step_ops, rho)
+            st.run(step_ops, width=-1)
+            zz = st.expect_z([0b11])[0]
+            worst = max(worst, abs(zz - O.expect_z(rho, 0b11)))
+        assert worst < tol, worst
+        assert abs(st.trace() - 1) < (TOL64 if precision == "fp64" else 1e-5)
+
+
+def test_readouts(tq):
+    n = 7
+    rho = random_general_matrix(n, 9)
+    masks = list(range(1, 21)) + [(1 << n) - 1]       # > 16 masks: several reduction launches
+    with tq.State(n, "fp64") as st:
+        st.set_rho(rho)
+        tr = st.trace()
+        zs = st.expect_z(masks)
+        p = st.probs()
+    assert abs(tr - O.trace(rho)) < TOL64
+    assert maxabs(zs, [O.expect_z(rho, m) for m in masks]) < TOL64
+    assert maxabs(p, O.probabilities(rho)) < TOL64
+
+
+def test_split_readouts_are_renormalised(tq):
+    n = 5
+    rho = W.random_density_matrix(n, 2) * 1.5     # trace 1.5: readouts divide by it
+    with tq.State(n, "split") as st:
+        st.set_rho(rho)
+        assert abs(st.trace() - 1.5) < 1e-6
+        zs = st.expect_z([1, 6, 31])
+        p = st.probs()
+    want = [O.expect_z(rho, m) / 1.5 for m in (1, 6, 31)]
+    assert maxabs(zs, want) < 1e-6
+    assert abs(np.sum(p) - 1) < 1e-6
+
+
+def test_edge_cases(tq):
+    # one qubit; a block as wide as the register (a single group); empty circuit
+    for n, k in [(1, 1), (2, 2), (3, 3), (4, 4)]:
+        rho = random_general_matrix(n, 30 + n)
+        Ks = W.random_kraus(k, 3, 50 + n)
+        want = O.apply_kraus(rho, Ks, list(range(k))[::-1])
+        for precision, tol in [("fp64", TOL64), ("split", 2e-6)]:
+            with tq.State(n, precision) as st:
+                st.set_rho(rho)
+                st.apply_kraus(list(range(k))[::-1], Ks)
+                assert maxabs(st.rho(), want) < tol
+    with tq.State(3, "fp64") as st:
+        assert st.run([], width=2) == 0
+        assert abs(st.rho()[0, 0] - 1) == 0
+        st.run(W.ghz(3), width=2)
+        before = st.rho()
+        for bad in ([("h", [3], ())], [("cx", [1, 1], ())], [("depol", [0], (2.0,))],
+                    [("thermal", [0], (1e-6, 1e-6, 5e-6))]):
+            with pytest.raises(tq.TqError):
+                st.run(bad, width=2)
+        with pytest.raises(tq.TqError) as e:
+            st.apply_gate([5], np.eye(2))
+        assert e.value.status == 2                     # TQ_ERR_QUBIT
+        assert maxabs(st.rho(), before) == 0           # errors leave the state unchanged
+        st.reset()
+        assert st.rho()[0, 0] == 1 and abs(st.trace() - 1) == 0
+
+
+def test_ghz_depolarizing_closed_form_at_12q(tq):
+    n, p = 12, 0.03
+    ops = W.ghz(n) + [("depol", [q], (p,)) for q in range(n)]
+    with tq.State(n, "fp64") as st:
+        st.run(ops, width=-1)
+        zz = st.expect_z([0b11, (1 << 11) | 1, 1 << 5])
+    assert abs(zz[0] - (1 - p) ** 2) < TOL64
+    assert abs(zz[1] - (1 - p) ** 2) < TOL64
+    assert abs(zz[2]) < TOL64
+
+
+def _factorised_check(tq, n, subset, width, precision, n_gates, seed, n_samples=4096, tol=TOL64):
+    """Full-size check: a product state (random SU(2) + amplitude damping on
+    every qubit), then a noisy circuit on `subset` only. rho factorises into
+    the oracle's small results, so sampled entries of the 4^n vector can be
+    computed one by one."""
+    import torch
+
+    prefix = W.product_prefix(n, seed)
+    sub = W.random_noisy_circuit(len(subset), n_gates, seed + 1, gate_set=("h", "rz", "cx", "su2", "rzz"))
+    body = [(name, [subset[q] for q in qs], params) for name, qs, params in sub.ops]
+    # oracle pieces
+    factors = {}
+    for q in range(n):
+        if q not in subset:
+            ops_q = [(nm, [0], pr) for nm, qs, pr in prefix if qs == [q]]
+            factors[q] = O.run_circuit(1, ops_q)
+    local = {q: j for j, q in enumerate(subset)}
+    ops_s = [(nm, [local[qs[0]]], pr) for nm, qs, pr in prefix if qs[0] in local] + sub.ops
+    rho_s = O.run_circuit(len(subset), ops_s)
+
+    with tq.State(n, precision) as st:
+        st.run(prefix + body, width=width)
+        tr = st.trace()
+        vec = st._buf.view(torch.complex128 if precision == "fp64" else torch.complex64)
+        N = 1 << n
+        rng = np.random.default_rng(seed)
+        r = rng.integers(0, N, n_samples)
+        c = rng.integers(0, N, n_samples)
+        r[:3] = [0, N - 1, 0]
+        c[:3] = [0, N - 1, N - 1]
+        idx = torch.as_tensor(r + c * N, device="cuda")
+        got = vec[idx].cpu().numpy().astype(np.complex128)
+    want = np.empty(n_samples, dtype=np.complex128)
+    for s in range(n_samples):
+        rs = sum(((int(r[s]) >> q) & 1) << j for j, q in enumerate(subset))
+        cs = sum(((int(c[s]) >> q) & 1) << j for j, q in enumerate(subset))
+        v = rho_s[rs, cs]
+        for q, f in factors.items():
+            v *= f[(int(r[s]) >> q) & 1, (int(c[s]) >> q) & 1]
+        want[s] = v
+    assert abs(tr - 1) < (1e-11 if precision == "fp64" else 1e-5)
+    err = float(np.max(np.abs(got - want)))
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("width", [0, 1, 2, 3, 4])
+def test_full_size_12q_factorised(tq, width):
+    _factorised_check(tq, 12, [0, 5, 10, 11], width, "fp64", 40, 12)
+
+
+def test_full_size_15q_factorised_fp64(tq):
+    # the 15-qubit register in the launch configuration of the benchmark
+    _factorised_check(tq, 15, [0, 6, 13, 14], -1, "fp64", 12, 15)
+
+
+def test_full_size_15q_factorised_split(tq):
+    _factorised_check(tq, 15, [1, 7, 12, 14], -1, "split", 30, 16, tol=2e-6)
