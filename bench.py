@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark: noisy density-matrix evolution of a 15-qubit ring transverse-
+field Ising Trotter circuit on one GB300 (sm_103a).
+
+One step = one Trotter step (30 noisy gates: 15 RZZ(0.2) with 2-qubit
+depolarising 5e-4 on the ring, 15 RX(0.1) with 1-qubit depolarising 5e-4)
+through the whole hot path -- superoperator build (FP64, GPU), fusion (FP64,
+GPU), apply passes over all 4^15 entries of vec(rho), and the FP64 <Z0 Z1>
+reduction -- with rho carried from step to step.
+
+  value      noisy gates/s of the FP64 path, inputs resident in device memory
+             (a compiled program re-run each step; readout to device memory)
+  e2e        the same through the public C-ABI call with host buffers: each
+             step copies the step's op tables host-to-device (tq_run_circuit)
+             and reads <Z0 Z1> back to the host (tq_expect_z)
+  split      the split-precision path (complex64 rho, FP32 products, FP64
+             build/fusion/reductions) on the same workload, with its error
+             against the FP64 path
+  roofline   dominant kernel of the FP64 path (and of the split path),
+             algorithmic flops or bytes per launch over CUDA-event-timed
+             launch durations inside the timed region
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (see cpu_baseline())
+
+--impl reference times the CPU oracle (there is no reference code) on the
+same workload and metric, one bounded sample per step.
+
+Multi-GPU: the path does not shard (one 16 GiB density matrix per GPU); with
+--gpus N each rank runs an independent replica and value sums the ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "superoperator gates/s at 15q (FP64 vs split), served circuits/s + p99 latency"
+UNIT = "noisy gates/s"
+N_QUBITS = 15
+ZZ_MASK = 0b11
+SAMPLE_QUBITS = 12      # register size of the CPU-oracle sample
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    # GB300 FP64 (DFMA) rate: 1.25 TFLOP/s nominal at 2070 MHz on 152 SMs,
+    # i.e. 4 FP64 flops (2 DFMA) per SM per clock.
+    return 152 * 4 * sm_mhz * 1e6 / 1e12
+
+
+def traffic_from_profile(kernel: str):
+    """dram read+write bytes per launch from the committed ncu summary of
+    `kernel`, if the kernel source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.txt")
+    src = os.path.join(ROOT, "paper_2404_13184_gb300", "csrc", "tq_apply.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256_16") != sha:
+            return None
+        return float(fields["dram_bytes_per_full_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def step_ops():
+    from paper_2404_13184_gb300 import workloads
+    return workloads.tfim_ring(N_QUBITS, steps=1).ops
+
+
+def run_device_leg(tq, torch, precision, steps, warmup, world, clocks=None):
+    """K timed steps from device-resident inputs; returns timings and stats."""
+    import torch.distributed as dist
+    st = tq.State(N_QUBITS, precision)
+    prog = tq.DeviceProgram(N_QUBITS, step_ops(), width=-1, precision=precision)
+    masks = torch.tensor([ZZ_MASK], dtype=torch.int64, device="cuda")
+    out = torch.zeros(warmup + steps, dtype=torch.float64, device="cuda")
+    for w in range(warmup):
+        st.run_program(prog)
+        st.expect_z_device(masks.data_ptr(), 1, out[w:].data_ptr())
+    torch.cuda.synchronize()
+    st.profile(True)
+    launches0 = st.launch_count()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0.record(stream)
+    for i in range(steps):
+        st.run_program(prog)
+        st.expect_z_device(masks.data_ptr(), 1, out[warmup + i:].data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = st.launch_count() - launches0
+    stats = st.profile_stats()
+    st.profile(False)
+    zz = out.cpu().tolist()
+    res = {"ms": ms, "launches": launches, "stats": stats, "zz": zz, "blocks": prog.n_blocks,
+           "max_width": prog.max_width, "table_bytes": prog.table_bytes, "clocks": clk}
+    prog.free()
+    st.free()
+    return res
+
+
+def run_e2e_leg(tq, torch, precision, steps, warmup, world):
+    """The public host-buffer API: tq_run_circuit + tq_expect_z per step."""
+    import torch.distributed as dist
+    st = tq.State(N_QUBITS, precision)
+    prog = tq.Program(step_ops())
+    for _ in range(warmup):
+        st.run(prog, width=-1)
+        st.expect_z([ZZ_MASK])
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.run(prog, width=-1)
+        st.expect_z([ZZ_MASK])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    st.free()
+    return dt * 1e3
+
+
+def dominant(stats: dict):
+    apply = {k: v for k, v in stats.items() if k.startswith("apply")}
+    name = max(apply, key=lambda k: apply[k]["total_ms"])
+    return name, apply[name]
+
+
+def cpu_sample_rate(pairs: int = 1):
+    """Oracle rate on a bounded sample of the workload: `pairs` x (RZZ + 2q
+    depolarising, RX + 1q depolarising) of the ring TFIM step, on a
+    SAMPLE_QUBITS-qubit register, scaled by 4^-(15 - SAMPLE_QUBITS) to the
+    15-qubit register (the oracle's cost per op is proportional to 4^n).
+    Returns (scaled gates/s, raw gates/s, seconds)."""
+    import numpy as np
+    from oracle import dm_oracle
+    from paper_2404_13184_gb300 import workloads
+    n = SAMPLE_QUBITS
+    ops = workloads.tfim_ring(n, steps=1).ops
+    pair_ops = ops[0:2] + ops[2 * n:2 * n + 2]
+    rho = dm_oracle.zero_state(n)
+    t0 = time.perf_counter()
+    for _ in range(pairs):
+        for op in pair_ops:
+            rho = dm_oracle.apply_op(rho, op)
+    dt = time.perf_counter() - t0
+    raw = 2 * pairs / dt
+    return raw * 4.0 ** (-(N_QUBITS - n)), raw, dt
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_sample_rate(1)
+    total_gates, total_s = 0, 0.0
+    for _ in range(args.steps):
+        _, raw, dt = cpu_sample_rate(1)
+        total_gates += 2
+        total_s += dt
+    raw = total_gates / total_s
+    value = raw * 4.0 ** (-(N_QUBITS - SAMPLE_QUBITS))
+    sample = (f"per step: RZZ+2q depolarising and RX+1q depolarising of the ring TFIM on a {SAMPLE_QUBITS}-qubit "
+              f"register, rate scaled by 4^-{N_QUBITS - SAMPLE_QUBITS} to 15 qubits (oracle cost per op ~ 4^n)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tfim-ring-15q", "n_qubits": N_QUBITS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "raw_value_at_sample_size": raw},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tanq", choices=["tanq", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 leg (default --steps)")
+    ap.add_argument("--n-qubits", type=int, default=15, help="register size (15 for the benchmark; smaller "
+                    "registers for profiling captures)")
+    args = ap.parse_args()
+    global N_QUBITS
+    N_QUBITS = args.n_qubits
+    if args.warmup < 3 and args.impl != "reference":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2404_13184_gb300 import binding as tq
+    tq.load()
+    hbm_gbs, sm_max_cfg, peak_src = peaks()
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis and vis.split(",")[0].strip().isdigit():
+        gpu_index = int(vis.split(",")[local].strip())
+
+    K, W = args.steps, args.warmup
+    K64 = args.fp64_steps or K
+    gates_per_step = 2 * N_QUBITS
+    fp64 = run_device_leg(tq, torch, "fp64", K64, W, world, Clocks(gpu_index))
+    split = None if args.no_split else run_device_leg(tq, torch, "split", K, W, world)
+    e2e_ms = None if args.no_e2e else run_e2e_leg(tq, torch, "fp64", K64, W, world)
+
+    def max_over_ranks(v):
+        if world == 1 or v is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms64 = max_over_ranks(fp64["ms"])
+    value = world * K64 * gates_per_step / (ms64 / 1e3)
+    clk = fp64["clocks"] or {}
+    sm_mhz = clk.get("sm_mhz") or sm_max_cfg
+    name64, st64 = dominant(fp64["stats"])
+    ach64 = st64["flops"] * st64["launches"] / (st64["total_ms"] / 1e3) / 1e12
+    peak64 = fp64_peak_tflops(sm_max_cfg)
+    roof = {"kernel": name64, "bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+            "frac": ach64 / peak64, "traffic": traffic_from_profile(name64),
+            "algorithmic_bytes_per_launch": st64["bytes"], "algorithmic_flops_per_launch": st64["flops"],
+            "launches": st64["launches"], "avg_launch_ms": st64["total_ms"] / st64["launches"],
+            "peak_source": "DFMA pipe: 152 SMs x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
+            "frac_at_measured_clock": ach64 / fp64_peak_tflops(sm_mhz)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K64, "warmup": W,
+            "ms_per_step": ms64 / K64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tfim-ring-{N_QUBITS}q: per step {N_QUBITS} x (RZZ(0.2) + 2q depolarising 5e-4) "
+                                   f"on the ring and {N_QUBITS} x (RX(0.1) + 1q depolarising 5e-4), <Z0 Z1> after "
+                                   "each step",
+                       "n_qubits": N_QUBITS, "rho_bytes": 16 << (2 * N_QUBITS), "fusion": "auto",
+                       "precision": "fp64 (split path in the 'split' object)",
+                       "fp64_blocks_per_step": fp64["blocks"], "fp64_max_width": fp64["max_width"],
+                       "l2": "inputs larger than L2 (16 GiB rho), no flush", "parallelism": "replicas"
+                       if world > 1 else "single"},
+            "roofline": roof, "gpu_launches": fp64["launches"],
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons", []), "samples": clk.get("samples")},
+            "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)}
+                        for k, v in fp64["stats"].items()}}
+    if e2e_ms is not None:
+        e2e_ms = max_over_ranks(e2e_ms)
+        line["e2e"] = {"value": world * K64 * gates_per_step / (e2e_ms / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": fp64["table_bytes"] + 8, "d2h_bytes_per_step": 3 * 8,
+                       "ms_per_step": e2e_ms / K64}
+    if split is not None:
+        mss = max_over_ranks(split["ms"])
+        vs = world * K * gates_per_step / (mss / 1e3)
+        ns, ss = dominant(split["stats"])
+        ach = ss["bytes"] * ss["launches"] / (ss["total_ms"] / 1e3) / 1e9
+        n_cmp = min(len(split["zz"]), len(fp64["zz"]))
+        err = max(abs(a - b) for a, b in zip(split["zz"][:n_cmp], fp64["zz"][:n_cmp]))
+        line["split"] = {"value": vs, "unit": UNIT, "ms_per_step": mss / K, "steps": K, "dtype": "f32",
+                         "speedup_vs_fp64": vs / value, "blocks_per_step": split["blocks"],
+                         "max_width": split["max_width"], "zz_max_abs_err_vs_fp64": err,
+                         "roofline": {"kernel": ns, "bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+                                      "frac": ach / hbm_gbs, "traffic": traffic_from_profile(ns),
+                                      "algorithmic_bytes_per_launch": ss["bytes"], "launches": ss["launches"],
+                                      "avg_launch_ms": ss["total_ms"] / ss["launches"],
+                                      "peak_source": f"{peak_src} HBM copy bandwidth"},
+                         "gpu_launches": split["launches"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scaled, raw, dt = cpu_sample_rate(2)
+        line["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"2 x (RZZ+2q depolarising, RX+1q depolarising) of the ring TFIM on a "
+                                          f"{SAMPLE_QUBITS}-qubit register ({dt:.1f} s, {raw:.3g} gates/s), scaled by "
+                                          f"4^-{N_QUBITS - SAMPLE_QUBITS} to 15 qubits (oracle cost per op ~ 4^n)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -191,6 +191,57 @@ tq_status tq_expect_z(tq_state* s, const uint64_t* masks, int n_masks, double* o
  * qubit in the computational basis (renormalised to sum 1 in TQ_SPLIT). */
 tq_status tq_probs(tq_state* s, double* out);
 
+/* ---- compiled programs (ops resident in device memory) ------------------ */
+
+typedef struct tq_program tq_program; /* opaque; owns device copies of its tables */
+
+/* Validate ops for an n-qubit register of the given precision, plan the
+ * fusion (max_fuse_width as in tq_run_circuit) and upload the Kraus sets and
+ * plan tables to device memory once (synchronously). Running the program
+ * then re-does the superoperator build, the fusion and the apply passes from
+ * device-resident inputs with no host copies. */
+tq_status tq_program_create(int n_qubits, int precision, const tq_op* ops, size_t n_ops,
+                            int max_fuse_width, tq_program** out);
+
+/* Enqueue the program on the state's stream (asynchronous). The state must
+ * have the program's n and precision (TQ_ERR_ARG otherwise). One program
+ * may be run on several states, but not concurrently on two streams. */
+tq_status tq_program_run(tq_state* s, const tq_program* p);
+
+/* Number of ops, of fused blocks, widest block, and the bytes of its device
+ * tables (Kraus sets and plan: what tq_run_circuit copies host-to-device
+ * for the same ops). Any output pointer may be NULL. */
+tq_status tq_program_info(const tq_program* p, size_t* n_ops, size_t* n_blocks, int* max_width,
+                          size_t* table_bytes);
+
+void tq_program_free(tq_program* p);
+
+/* Device-side readout: out_dev[i] = Re Tr(rho Z_{masks_dev[i]}) (divided by
+ * Re Tr rho in TQ_SPLIT) for i < n_masks <= 16; masks_dev and out_dev are
+ * device pointers. Asynchronous on the state's stream. */
+tq_status tq_expect_z_device(tq_state* s, const uint64_t* masks_dev, int n_masks, double* out_dev);
+
+/* ---- per-launch profiling (CUDA events on the state's stream) ---------- */
+
+typedef struct tq_kernel_stat {
+  char name[32];      /* e.g. "apply_f64_w2", "superop_build", "fuse", "reduce" */
+  uint64_t launches;
+  double total_ms;    /* sum of event-timed launch durations */
+  double flops;       /* algorithmic flops per launch (dense superoperator count) */
+  double bytes;       /* algorithmic HBM bytes per launch (read + write of rho) */
+} tq_kernel_stat;
+
+/* Turn event timing of every kernel launch on (1) or off (0); turning it on
+ * clears the statistics. */
+tq_status tq_profile_enable(tq_state* s, int on);
+
+/* Statistics since profiling was enabled, one entry per kernel kind (waits
+ * for the stream). *count receives the number of kinds (<= capacity filled). */
+tq_status tq_profile_read(tq_state* s, tq_kernel_stat* out, int capacity, int* count);
+
+/* Total kernels this state has launched since creation (always counted). */
+tq_status tq_launch_count(const tq_state* s, uint64_t* out);
+
 /* ---- host-side helpers (no GPU work; usable without a device) ----------- */
 
 /* Matrix of a named gate: *k_out = 1 or 2, U_out receives 2^k x 2^k complex

@@ -35,6 +35,11 @@ class TqOp(ctypes.Structure):
                 ("name", c_int32), ("params", c_double * 4), ("mats", POINTER(c_double))]
 
 
+class TqKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", c_uint64), ("total_ms", c_double),
+                ("flops", c_double), ("bytes", c_double)]
+
+
 class TqError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -59,6 +64,14 @@ _SIGNATURES = [
     ("tq_trace", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     ("tq_expect_z", c_int, [c_void_p, POINTER(c_uint64), c_int, POINTER(c_double)]),
     ("tq_probs", c_int, [c_void_p, POINTER(c_double)]),
+    ("tq_program_create", c_int, [c_int, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_void_p)]),
+    ("tq_program_run", c_int, [c_void_p, c_void_p]),
+    ("tq_program_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int), POINTER(c_size_t)]),
+    ("tq_program_free", None, [c_void_p]),
+    ("tq_expect_z_device", c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    ("tq_profile_enable", c_int, [c_void_p, c_int]),
+    ("tq_profile_read", c_int, [c_void_p, POINTER(TqKernelStat), c_int, POINTER(c_int)]),
+    ("tq_launch_count", c_int, [c_void_p, POINTER(c_uint64)]),
     ("tq_gate_matrix", c_int, [c_int, POINTER(c_double), POINTER(c_int), POINTER(c_double)]),
     ("tq_channel_kraus", c_int, [c_int, c_int, POINTER(c_double), c_int, POINTER(c_int), POINTER(c_double)]),
     ("tq_plan_fusion", c_int, [c_int, POINTER(TqOp), c_size_t, c_int, c_int, POINTER(c_int), POINTER(c_int),
@@ -128,6 +141,33 @@ class Program:
                 o.mats = _dptr(m)
             else:
                 raise ValueError(f"unknown op {name!r}")
+
+
+class DeviceProgram:
+    """A circuit planned and uploaded to device memory once (tq_program)."""
+
+    def __init__(self, n: int, ops, width: int = -1, precision: str = "fp64"):
+        lib = load()
+        prog = ops if isinstance(ops, Program) else Program(ops)
+        self.n, self.precision = n, precision
+        self._h = c_void_p()
+        _check(lib.tq_program_create(n, PRECISION[precision], prog.arr, prog.n_ops, width, ctypes.byref(self._h)),
+               "tq_program_create")
+        no, nb, mw, tb = c_size_t(0), c_size_t(0), c_int(0), c_size_t(0)
+        _check(lib.tq_program_info(self._h, ctypes.byref(no), ctypes.byref(nb), ctypes.byref(mw), ctypes.byref(tb)),
+               "tq_program_info")
+        self.n_ops, self.n_blocks, self.max_width, self.table_bytes = no.value, nb.value, mw.value, tb.value
+
+    def free(self):
+        if self._h:
+            _lib.tq_program_free(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def plan_fusion(n: int, ops, width: int, precision: str = "fp64"):
@@ -229,6 +269,29 @@ class State:
         nb = c_size_t(0)
         _check(_lib.tq_run_circuit(self._h, prog.arr, prog.n_ops, width, ctypes.byref(nb)), "tq_run_circuit")
         return nb.value
+
+    def run_program(self, prog: "DeviceProgram"):
+        _check(_lib.tq_program_run(self._h, prog._h), "tq_program_run")
+
+    def expect_z_device(self, masks_dev_ptr: int, n_masks: int, out_dev_ptr: int):
+        _check(_lib.tq_expect_z_device(self._h, c_void_p(masks_dev_ptr), n_masks, c_void_p(out_dev_ptr)),
+               "tq_expect_z_device")
+
+    def profile(self, on: bool = True):
+        _check(_lib.tq_profile_enable(self._h, 1 if on else 0), "tq_profile_enable")
+
+    def profile_stats(self) -> dict:
+        arr = (TqKernelStat * 16)()
+        cnt = c_int(0)
+        _check(_lib.tq_profile_read(self._h, arr, 16, ctypes.byref(cnt)), "tq_profile_read")
+        return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
+                                       "flops": float(arr[i].flops), "bytes": float(arr[i].bytes)}
+                for i in range(min(cnt.value, 16))}
+
+    def launch_count(self) -> int:
+        v = c_uint64(0)
+        _check(_lib.tq_launch_count(self._h, ctypes.byref(v)), "tq_launch_count")
+        return int(v.value)
 
     def apply_gate(self, qubits, U):
         q = (c_int * len(qubits))(*qubits)

@@ -76,8 +76,10 @@ cudaError_t launch_init_zero_state(void* rho, int n, int precision, cudaStream_t
 // Reductions over the diagonal: quantities [Re tr, Im tr, Re Tr(rho Z_mask_i)...]
 // partials: gridDim x nq doubles of scratch; out: nq doubles (device).
 int diag_reduce_grid(int n);
+int build_superops_launches(int n_ops);
 cudaError_t launch_diag_reduce(const void* rho, int n, int precision, const unsigned long long* masks,
-                               int n_masks, double* partials, double* out, bool normalize, cudaStream_t st);
+                               int n_masks, double* partials, double* out, bool normalize, double* masked_out,
+                               cudaStream_t st);
 cudaError_t launch_diag_probs(const void* rho, int n, int precision, const double* trace_or_null,
                               double* out, cudaStream_t st);
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t count, cudaStream_t st);

@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(kRedThreads) k_diag_partial(const T2* __restri
 
 // Sums the per-CTA partials in CTA order. With `normalize`, the masked sums
 // are divided by Re Tr(rho) (FP64 trace renormalisation of split states).
+// `masked_out` (optional) receives the masked sums alone.
 __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks, int nq, int normalize,
-                               double* __restrict__ out) {
+                               double* __restrict__ out, double* __restrict__ masked_out) {
   __shared__ double tot[kMaxQuant];
   const int q = threadIdx.x;
   if (q < nq) {
@@ -176,7 +177,11 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nblocks,
     tot[q] = s;
   }
   __syncthreads();
-  if (q < nq) out[q] = (normalize && q >= 2) ? tot[q] / tot[0] : tot[q];
+  if (q < nq) {
+    const double v = (normalize && q >= 2) ? tot[q] / tot[0] : tot[q];
+    out[q] = v;
+    if (masked_out && q >= 2) masked_out[q - 2] = v;
+  }
 }
 
 template <typename T2>
@@ -226,20 +231,23 @@ cudaError_t launch_init_zero_state(void* rho, int n, int precision, cudaStream_t
   return cudaGetLastError();
 }
 
+int build_superops_launches(int n_ops) { return (n_ops + 65534) / 65535; }
+
 int diag_reduce_grid(int n) {
   const long long N = 1ll << n;
   return (int)std::max(1ll, std::min(152ll, N / 512));
 }
 
 cudaError_t launch_diag_reduce(const void* rho, int n, int precision, const unsigned long long* masks,
-                               int n_masks, double* partials, double* out, bool normalize, cudaStream_t st) {
+                               int n_masks, double* partials, double* out, bool normalize, double* masked_out,
+                               cudaStream_t st) {
   if (n_masks < 0 || n_masks > 16) return cudaErrorInvalidValue;
   const int grid = diag_reduce_grid(n);
   if (precision == 0)
     k_diag_partial<double2><<<grid, kRedThreads, 0, st>>>((const double2*)rho, n, masks, n_masks, partials);
   else
     k_diag_partial<float2><<<grid, kRedThreads, 0, st>>>((const float2*)rho, n, masks, n_masks, partials);
-  k_reduce_final<<<1, 32, 0, st>>>(partials, grid, 2 + n_masks, normalize ? 1 : 0, out);
+  k_reduce_final<<<1, 32, 0, st>>>(partials, grid, 2 + n_masks, normalize ? 1 : 0, out, masked_out);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
-// States, circuit runs and readouts: the C-ABI entry points that do GPU
-// work. Host code here validates, plans fusion, packs tables and enqueues
-// kernels; every arithmetic step of the simulation runs on the device.
+// States, programs, circuit runs and readouts: the C-ABI entry points that
+// do GPU work. Host code here validates ops, plans fusion, packs tables and
+// enqueues kernels; every arithmetic step of the simulation runs on the
+// device (superoperator build and fusion in FP64, apply passes, reductions).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -25,7 +26,34 @@ struct PinBuf {
   size_t cap = 0;
 };
 
+// Kernel kinds for launch counting and event profiling.
+enum Kind { K_BUILD = 0, K_FUSE, K_REDUCE, K_APPLY64 /* +w-1 */, K_APPLY32 = K_APPLY64 + 4, K_NKINDS = K_APPLY32 + 4 };
+const char* kKindName[K_NKINDS] = {"superop_build", "fuse",         "reduce",       "apply_f64_w1",
+                                   "apply_f64_w2",  "apply_f64_w3", "apply_f64_w4", "apply_f32_w1",
+                                   "apply_f32_w2",  "apply_f32_w3", "apply_f32_w4"};
+
+struct Pending {
+  int kind;
+  cudaEvent_t e0, e1;
+};
+
 }  // namespace
+
+// A planned circuit: host-side launch parameters plus device tables.
+struct tq_program {
+  int n = 0;
+  int prec = 0;
+  size_t n_ops = 0;
+  int max_width = 0;
+  int max_dim2 = 0;
+  int n_work = 0;
+  std::vector<ApplyParams> params;  // per block
+  std::vector<long long> sb_off;    // per block, complex entries
+  // device tables (one blob: Kraus sets, op/block/member/work tables)
+  DevBuf blob, sops, sb64, sb32;
+  size_t o_kraus = 0, o_ops = 0, o_blk = 0, o_mem = 0, o_work = 0, blob_bytes = 0;
+  bool owns = true;  // standalone programs own their buffers
+};
 
 struct tq_state {
   int n = 0;
@@ -36,9 +64,18 @@ struct tq_state {
   size_t rho_bytes = 0;
   bool owns_rho = false;
   bool poisoned = false;
-  DevBuf upload, sops, sb64, sb32, red, probs, staging;
+  DevBuf red, probs, staging;
   PinBuf pin, pin_small;
   cudaEvent_t pin_free = nullptr;  // recorded after the last upload from `pin`
+  tq_program scratch;              // plan of the last tq_run_circuit call
+  uint64_t launches = 0;
+  bool prof_on = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  uint64_t prof_launches[K_NKINDS] = {};
+  double prof_ms[K_NKINDS] = {};
+  double prof_flops[K_NKINDS] = {};
+  double prof_bytes[K_NKINDS] = {};
 };
 
 namespace {
@@ -53,24 +90,28 @@ tq_status cuda_fail(tq_state* s, cudaError_t e) {
   return TQ_ERR_CUDA;
 }
 
-// Grow a device buffer; the old contents are not kept. Waits for the stream
+// Grow a device buffer (contents not kept). With a stream, waits for it
 // first because queued kernels may still read the old buffer.
-tq_status ensure(tq_state* s, DevBuf& b, size_t bytes) {
-  if (b.cap >= bytes) return TQ_OK;
-  cudaError_t e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return cuda_fail(s, e);
+cudaError_t grow(DevBuf& b, size_t bytes, cudaStream_t wait_on, bool sync) {
+  if (b.cap >= bytes) return cudaSuccess;
+  if (sync) {
+    cudaError_t e = cudaStreamSynchronize(wait_on);
+    if (e != cudaSuccess) return e;
+  }
   if (b.ptr) cudaFree(b.ptr);
   b.ptr = nullptr;
   b.cap = 0;
   const size_t want = align_up(std::max<size_t>(bytes, 4096), 4096);
-  e = cudaMalloc(&b.ptr, want);
+  cudaError_t e = cudaMalloc(&b.ptr, want);
   if (e != cudaSuccess) {
     b.ptr = nullptr;
-    return cuda_fail(s, e);
+    return e;
   }
   b.cap = want;
-  return TQ_OK;
+  return cudaSuccess;
 }
+
+tq_status ensure(tq_state* s, DevBuf& b, size_t bytes) { return cuda_fail(s, grow(b, bytes, s->stream, true)); }
 
 tq_status ensure_pinned(tq_state* s, PinBuf& b, size_t bytes) {
   if (b.cap >= bytes) return TQ_OK;
@@ -87,6 +128,12 @@ tq_status ensure_pinned(tq_state* s, PinBuf& b, size_t bytes) {
   return TQ_OK;
 }
 
+void free_buf(DevBuf& b) {
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.cap = 0;
+}
+
 size_t entry_bytes(int prec) { return prec == TQ_FP64 ? 16 : 8; }
 
 tq_status check_state(tq_state* s) {
@@ -95,108 +142,56 @@ tq_status check_state(tq_state* s) {
   return TQ_OK;
 }
 
-tq_status create_impl(int n, int precision, void* stream, void* ext, size_t ext_bytes, tq_state** out) {
-  if (!out) return TQ_ERR_ARG;
-  *out = nullptr;
-  if (n < 1 || n > kMaxQubits) return TQ_ERR_ARG;
-  if (precision != TQ_FP64 && precision != TQ_SPLIT) return TQ_ERR_ARG;
-  tq_state* s = new (std::nothrow) tq_state();
-  if (!s) return TQ_ERR_OOM;
-  s->n = n;
-  s->prec = precision;
-  s->stream = static_cast<cudaStream_t>(stream);
-  s->rho_bytes = entry_bytes(precision) << (2 * n);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) {
-    delete s;
-    return TQ_ERR_CUDA;
-  }
-  if (ext) {
-    if (ext_bytes < s->rho_bytes || (reinterpret_cast<uintptr_t>(ext) & 255)) {
-      delete s;
-      return TQ_ERR_ARG;
+// ---- launch accounting -------------------------------------------------
+
+// Run `launch` (which enqueues `count` kernels of one kind on s->stream),
+// bracketed by events when profiling is on.
+template <typename F>
+cudaError_t timed(tq_state* s, int kind, int count, F launch) {
+  Pending pd{kind, nullptr, nullptr};
+  if (s->prof_on) {
+    for (cudaEvent_t* ev : {&pd.e0, &pd.e1}) {
+      if (!s->event_pool.empty()) {
+        *ev = s->event_pool.back();
+        s->event_pool.pop_back();
+      } else {
+        cudaError_t e = cudaEventCreate(ev);
+        if (e != cudaSuccess) return e;
+      }
     }
-    s->rho = ext;
-    s->owns_rho = false;
-  } else {
-    e = cudaMalloc(&s->rho, s->rho_bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      delete s;
-      return e == cudaErrorMemoryAllocation ? TQ_ERR_OOM : TQ_ERR_CUDA;
-    }
-    s->owns_rho = true;
+    cudaEventRecord(pd.e0, s->stream);
   }
-  e = cudaEventCreateWithFlags(&s->pin_free, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = launch_init_zero_state(s->rho, n, precision, s->stream);
-  if (e != cudaSuccess) {
-    tq_free(s);
-    return TQ_ERR_CUDA;
+  cudaError_t e = launch();
+  s->launches += count;
+  if (s->prof_on) {
+    cudaEventRecord(pd.e1, s->stream);
+    s->pending.push_back(pd);
+    s->prof_launches[kind] += count;
   }
-  *out = s;
-  return TQ_OK;
+  return e;
 }
 
-// Host tables of one circuit run, packed into a single upload.
-struct RunPlan {
+void fold_pending(tq_state* s) {
+  for (const Pending& pd : s->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pd.e0, pd.e1) == cudaSuccess) s->prof_ms[pd.kind] += ms;
+    s->event_pool.push_back(pd.e0);
+    s->event_pool.push_back(pd.e1);
+  }
+  s->pending.clear();
+}
+
+// ---- planning ------------------------------------------------------------
+
+struct HostTables {
   std::vector<double2> kraus;
   std::vector<OpDesc> ops;
   std::vector<BlockDesc> blocks;
   std::vector<MemberDesc> members;
   std::vector<FuseWork> work;
-  std::vector<Block> plan;
   long long sop_entries = 0;
   long long sb_entries = 0;
-  int max_dim2 = 0;
 };
-
-tq_status build_plan(int n, int prec, const tq_op* ops, size_t n_ops, int width, RunPlan* rp) {
-  std::vector<std::vector<int>> qs(n_ops);
-  rp->ops.resize(n_ops);
-  for (size_t i = 0; i < n_ops; ++i) {
-    tq_status st = validate_op(n, ops[i]);
-    if (st != TQ_OK) return st;
-    ResolvedOp r;
-    st = resolve_op(ops[i], &r);
-    if (st != TQ_OK) return st;
-    qs[i].assign(ops[i].qubits, ops[i].qubits + ops[i].k);
-    OpDesc& od = rp->ops[i];
-    od.k = r.k;
-    od.m = r.m;
-    od.kraus_off = (long long)rp->kraus.size();
-    od.sop_off = rp->sop_entries;
-    for (const cplx& v : r.kraus) rp->kraus.push_back(make_double2(v.real(), v.imag()));
-    const long long d2 = 1ll << (2 * r.k);
-    rp->sop_entries += d2 * d2;
-    rp->max_dim2 = std::max<int>(rp->max_dim2, (int)(d2 * d2));
-  }
-  tq_status st = plan_fusion(n, qs, width, prec, &rp->plan);
-  if (st != TQ_OK) return st;
-  for (size_t b = 0; b < rp->plan.size(); ++b) {
-    const Block& B = rp->plan[b];
-    BlockDesc bd{};
-    bd.width = B.width;
-    bd.n_members = (int)B.ops.size();
-    bd.member_off = (int)rp->members.size();
-    bd.sb_off = rp->sb_entries;
-    const int D = 1 << (2 * B.width);
-    rp->sb_entries += (long long)D * D;
-    for (int oi : B.ops) {
-      MemberDesc md{};
-      md.op = oi;
-      md.k = ops[oi].k;
-      for (int j = 0; j < md.k; ++j)
-        md.pos[j] = (int)(std::find(B.qubits, B.qubits + B.width, ops[oi].qubits[j]) - B.qubits);
-      rp->members.push_back(md);
-    }
-    rp->blocks.push_back(bd);
-    const int C = std::min(D, 1024 / D);
-    for (int c0 = 0; c0 < D; c0 += C) rp->work.push_back(FuseWork{(int)b, c0});
-  }
-  return TQ_OK;
-}
 
 ApplyParams apply_params(int n, const Block& B) {
   ApplyParams p{};
@@ -226,81 +221,215 @@ ApplyParams apply_params(int n, const Block& B) {
   return p;
 }
 
-template <typename T>
-T* section(char* base, size_t& off, size_t count) {
-  T* p = reinterpret_cast<T*>(base + off);
-  off = align_up(off + count * sizeof(T), 256);
-  return p;
+// Validate, resolve and plan `ops` into P's host fields and `t`.
+tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t) {
+  if (width < -1 || width > kMaxWidth) return TQ_ERR_ARG;
+  std::vector<std::vector<int>> qs(n_ops);
+  t->ops.resize(n_ops);
+  P->max_dim2 = 0;
+  for (size_t i = 0; i < n_ops; ++i) {
+    tq_status st = validate_op(n, ops[i]);
+    if (st != TQ_OK) return st;
+    ResolvedOp r;
+    st = resolve_op(ops[i], &r);
+    if (st != TQ_OK) return st;
+    qs[i].assign(ops[i].qubits, ops[i].qubits + ops[i].k);
+    OpDesc& od = t->ops[i];
+    od.k = r.k;
+    od.m = r.m;
+    od.kraus_off = (long long)t->kraus.size();
+    od.sop_off = t->sop_entries;
+    for (const cplx& v : r.kraus) t->kraus.push_back(make_double2(v.real(), v.imag()));
+    const long long d2 = 1ll << (2 * r.k);
+    t->sop_entries += d2 * d2;
+    P->max_dim2 = std::max<int>(P->max_dim2, (int)(d2 * d2));
+  }
+  std::vector<Block> plan;
+  tq_status st = plan_fusion(n, qs, width, prec, &plan);
+  if (st != TQ_OK) return st;
+  P->n = n;
+  P->prec = prec;
+  P->n_ops = n_ops;
+  P->max_width = 0;
+  P->params.clear();
+  P->sb_off.clear();
+  for (size_t b = 0; b < plan.size(); ++b) {
+    const Block& B = plan[b];
+    BlockDesc bd{};
+    bd.width = B.width;
+    bd.n_members = (int)B.ops.size();
+    bd.member_off = (int)t->members.size();
+    bd.sb_off = t->sb_entries;
+    const int D = 1 << (2 * B.width);
+    t->sb_entries += (long long)D * D;
+    for (int oi : B.ops) {
+      MemberDesc md{};
+      md.op = oi;
+      md.k = ops[oi].k;
+      for (int j = 0; j < md.k; ++j)
+        md.pos[j] = (int)(std::find(B.qubits, B.qubits + B.width, ops[oi].qubits[j]) - B.qubits);
+      t->members.push_back(md);
+    }
+    t->blocks.push_back(bd);
+    const int C = std::min(D, 1024 / D);
+    for (int c0 = 0; c0 < D; c0 += C) t->work.push_back(FuseWork{(int)b, c0});
+    P->params.push_back(apply_params(n, B));
+    P->sb_off.push_back(bd.sb_off);
+    P->max_width = std::max(P->max_width, B.width);
+  }
+  P->n_work = (int)t->work.size();
+  size_t off = 0;
+  P->o_kraus = off; off = align_up(off + t->kraus.size() * sizeof(double2), 256);
+  P->o_ops = off;   off = align_up(off + t->ops.size() * sizeof(OpDesc), 256);
+  P->o_blk = off;   off = align_up(off + t->blocks.size() * sizeof(BlockDesc), 256);
+  P->o_mem = off;   off = align_up(off + t->members.size() * sizeof(MemberDesc), 256);
+  P->o_work = off;  off = align_up(off + t->work.size() * sizeof(FuseWork), 256);
+  P->blob_bytes = std::max<size_t>(off, 256);
+  return TQ_OK;
+}
+
+void pack_blob(const tq_program& P, const HostTables& t, char* h) {
+  std::memcpy(h + P.o_kraus, t.kraus.data(), t.kraus.size() * sizeof(double2));
+  std::memcpy(h + P.o_ops, t.ops.data(), t.ops.size() * sizeof(OpDesc));
+  std::memcpy(h + P.o_blk, t.blocks.data(), t.blocks.size() * sizeof(BlockDesc));
+  std::memcpy(h + P.o_mem, t.members.data(), t.members.size() * sizeof(MemberDesc));
+  std::memcpy(h + P.o_work, t.work.data(), t.work.size() * sizeof(FuseWork));
+}
+
+// Enqueue superoperator build, fusion and every apply pass of P on s.
+tq_status enqueue_program(tq_state* s, const tq_program& P) {
+  if (P.n_ops == 0) return TQ_OK;
+  char* d = static_cast<char*>(P.blob.ptr);
+  const double2* d_kraus = reinterpret_cast<const double2*>(d + P.o_kraus);
+  const OpDesc* d_ops = reinterpret_cast<const OpDesc*>(d + P.o_ops);
+  const BlockDesc* d_blk = reinterpret_cast<const BlockDesc*>(d + P.o_blk);
+  const MemberDesc* d_mem = reinterpret_cast<const MemberDesc*>(d + P.o_mem);
+  const FuseWork* d_work = reinterpret_cast<const FuseWork*>(d + P.o_work);
+  double2* sops = static_cast<double2*>(P.sops.ptr);
+  double2* sb64 = static_cast<double2*>(P.sb64.ptr);
+  float2* sb32 = P.prec == TQ_SPLIT ? static_cast<float2*>(P.sb32.ptr) : nullptr;
+  cudaError_t e = timed(s, K_BUILD, build_superops_launches((int)P.n_ops), [&] {
+    return launch_build_superops(d_kraus, d_ops, (int)P.n_ops, P.max_dim2, sops, s->stream);
+  });
+  if (e == cudaSuccess)
+    e = timed(s, K_FUSE, 1, [&] { return launch_fuse(sops, d_ops, d_blk, d_mem, d_work, P.n_work, sb64, sb32, s->stream); });
+  const double entries = (double)(1ull << (2 * s->n));
+  for (size_t b = 0; b < P.params.size() && e == cudaSuccess; ++b) {
+    const ApplyParams& p = P.params[b];
+    const void* S = s->prec == TQ_FP64 ? (const void*)(sb64 + P.sb_off[b]) : (const void*)(sb32 + P.sb_off[b]);
+    const int kind = (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
+    e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream); });
+    if (s->prof_on) {
+      s->prof_flops[kind] = 8.0 * entries * (double)(1 << (2 * p.width));
+      s->prof_bytes[kind] = 2.0 * entries * (double)entry_bytes(s->prec);
+    }
+  }
+  return cuda_fail(s, e);
+}
+
+tq_status create_impl(int n, int precision, void* stream, void* ext, size_t ext_bytes, tq_state** out) {
+  if (!out) return TQ_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits) return TQ_ERR_ARG;
+  if (precision != TQ_FP64 && precision != TQ_SPLIT) return TQ_ERR_ARG;
+  tq_state* s = new (std::nothrow) tq_state();
+  if (!s) return TQ_ERR_OOM;
+  s->n = n;
+  s->prec = precision;
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->rho_bytes = entry_bytes(precision) << (2 * n);
+  s->scratch.owns = false;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete s;
+    return TQ_ERR_CUDA;
+  }
+  if (ext) {
+    if (ext_bytes < s->rho_bytes || (reinterpret_cast<uintptr_t>(ext) & 255)) {
+      delete s;
+      return TQ_ERR_ARG;
+    }
+    s->rho = ext;
+    s->owns_rho = false;
+  } else {
+    e = cudaMalloc(&s->rho, s->rho_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return e == cudaErrorMemoryAllocation ? TQ_ERR_OOM : TQ_ERR_CUDA;
+    }
+    s->owns_rho = true;
+  }
+  e = cudaEventCreateWithFlags(&s->pin_free, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = launch_init_zero_state(s->rho, n, precision, s->stream);
+  s->launches += 1;
+  if (e != cudaSuccess) {
+    tq_free(s);
+    return TQ_ERR_CUDA;
+  }
+  *out = s;
+  return TQ_OK;
 }
 
 tq_status run_impl(tq_state* s, const tq_op* ops, size_t n_ops, int width, size_t* n_blocks_out) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
   if (!ops && n_ops) return TQ_ERR_ARG;
-  if (width < -1 || width > kMaxWidth) return TQ_ERR_ARG;
   if (n_blocks_out) *n_blocks_out = 0;
   if (n_ops == 0) return TQ_OK;
-  RunPlan rp;
-  st = build_plan(s->n, s->prec, ops, n_ops, width, &rp);
+  tq_program plan;
+  HostTables t;
+  st = plan_program(s->n, s->prec, ops, n_ops, width, &plan, &t);
   if (st != TQ_OK) return st;
-
-  // layout of the upload blob (byte offsets; 256-byte aligned sections)
-  size_t off = 0;
-  const size_t o_kraus = off; off = align_up(off + rp.kraus.size() * sizeof(double2), 256);
-  const size_t o_ops = off;   off = align_up(off + rp.ops.size() * sizeof(OpDesc), 256);
-  const size_t o_blk = off;   off = align_up(off + rp.blocks.size() * sizeof(BlockDesc), 256);
-  const size_t o_mem = off;   off = align_up(off + rp.members.size() * sizeof(MemberDesc), 256);
-  const size_t o_work = off;  off = align_up(off + rp.work.size() * sizeof(FuseWork), 256);
-  const size_t blob = off;
-
-  if ((st = ensure(s, s->upload, blob)) != TQ_OK) return st;
-  if ((st = ensure(s, s->sops, rp.sop_entries * sizeof(double2))) != TQ_OK) return st;
-  if ((st = ensure(s, s->sb64, rp.sb_entries * sizeof(double2))) != TQ_OK) return st;
-  if (s->prec == TQ_SPLIT && (st = ensure(s, s->sb32, rp.sb_entries * sizeof(float2))) != TQ_OK) return st;
-
+  // reuse the state's scratch buffers for this plan
+  tq_program& P = s->scratch;
+  P.n = plan.n;
+  P.prec = plan.prec;
+  P.n_ops = plan.n_ops;
+  P.max_width = plan.max_width;
+  P.max_dim2 = plan.max_dim2;
+  P.n_work = plan.n_work;
+  P.params.swap(plan.params);
+  P.sb_off.swap(plan.sb_off);
+  P.o_kraus = plan.o_kraus; P.o_ops = plan.o_ops; P.o_blk = plan.o_blk; P.o_mem = plan.o_mem;
+  P.o_work = plan.o_work; P.blob_bytes = plan.blob_bytes;
+  if ((st = ensure(s, P.blob, P.blob_bytes)) != TQ_OK) return st;
+  if ((st = ensure(s, P.sops, t.sop_entries * sizeof(double2))) != TQ_OK) return st;
+  if ((st = ensure(s, P.sb64, t.sb_entries * sizeof(double2))) != TQ_OK) return st;
+  if (s->prec == TQ_SPLIT && (st = ensure(s, P.sb32, t.sb_entries * sizeof(float2))) != TQ_OK) return st;
   // the pinned staging buffer is reused: wait until its last upload finished
   cudaError_t e = cudaEventSynchronize(s->pin_free);
   if (e != cudaSuccess) return cuda_fail(s, e);
-  if ((st = ensure_pinned(s, s->pin, blob)) != TQ_OK) return st;
-  char* h = static_cast<char*>(s->pin.ptr);
-  std::memcpy(h + o_kraus, rp.kraus.data(), rp.kraus.size() * sizeof(double2));
-  std::memcpy(h + o_ops, rp.ops.data(), rp.ops.size() * sizeof(OpDesc));
-  std::memcpy(h + o_blk, rp.blocks.data(), rp.blocks.size() * sizeof(BlockDesc));
-  std::memcpy(h + o_mem, rp.members.data(), rp.members.size() * sizeof(MemberDesc));
-  std::memcpy(h + o_work, rp.work.data(), rp.work.size() * sizeof(FuseWork));
-  e = cudaMemcpyAsync(s->upload.ptr, h, blob, cudaMemcpyHostToDevice, s->stream);
+  if ((st = ensure_pinned(s, s->pin, P.blob_bytes)) != TQ_OK) return st;
+  pack_blob(P, t, static_cast<char*>(s->pin.ptr));
+  e = cudaMemcpyAsync(P.blob.ptr, s->pin.ptr, P.blob_bytes, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaEventRecord(s->pin_free, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e);
-
-  char* d = static_cast<char*>(s->upload.ptr);
-  const double2* d_kraus = reinterpret_cast<const double2*>(d + o_kraus);
-  const OpDesc* d_ops = reinterpret_cast<const OpDesc*>(d + o_ops);
-  const BlockDesc* d_blk = reinterpret_cast<const BlockDesc*>(d + o_blk);
-  const MemberDesc* d_mem = reinterpret_cast<const MemberDesc*>(d + o_mem);
-  const FuseWork* d_work = reinterpret_cast<const FuseWork*>(d + o_work);
-  double2* sops = static_cast<double2*>(s->sops.ptr);
-  double2* sb64 = static_cast<double2*>(s->sb64.ptr);
-  float2* sb32 = s->prec == TQ_SPLIT ? static_cast<float2*>(s->sb32.ptr) : nullptr;
-
-  e = launch_build_superops(d_kraus, d_ops, (int)rp.ops.size(), rp.max_dim2, sops, s->stream);
-  if (e == cudaSuccess)
-    e = launch_fuse(sops, d_ops, d_blk, d_mem, d_work, (int)rp.work.size(), sb64, sb32, s->stream);
-  for (size_t b = 0; b < rp.plan.size() && e == cudaSuccess; ++b) {
-    const ApplyParams p = apply_params(s->n, rp.plan[b]);
-    const void* S = s->prec == TQ_FP64 ? (const void*)(sb64 + rp.blocks[b].sb_off)
-                                       : (const void*)(sb32 + rp.blocks[b].sb_off);
-    e = launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(s, e);
-  if (n_blocks_out) *n_blocks_out = rp.plan.size();
-  return TQ_OK;
+  st = enqueue_program(s, P);
+  if (st == TQ_OK && n_blocks_out) *n_blocks_out = P.params.size();
+  return st;
 }
 
 // Reduction scratch: [16 masks][18 outputs][grid x 18 partials]
 constexpr size_t kRedMasks = 0, kRedOut = 256, kRedPartials = 512;
+constexpr size_t kRedBytes = kRedPartials + 152 * 18 * sizeof(double);
+
+tq_status reduce_device(tq_state* s, const unsigned long long* masks_dev, int n_masks, bool normalize,
+                        double* masked_out_dev) {
+  tq_status st = ensure(s, s->red, kRedBytes);
+  if (st != TQ_OK) return st;
+  char* d = static_cast<char*>(s->red.ptr);
+  cudaError_t e = timed(s, K_REDUCE, 2, [&] {
+    return launch_diag_reduce(s->rho, s->n, s->prec, masks_dev, n_masks, reinterpret_cast<double*>(d + kRedPartials),
+                              reinterpret_cast<double*>(d + kRedOut), normalize, masked_out_dev, s->stream);
+  });
+  return cuda_fail(s, e);
+}
 
 tq_status reduce_impl(tq_state* s, const unsigned long long* masks, int n_masks, bool normalize, double* host_out) {
-  tq_status st = ensure(s, s->red, kRedPartials + 152 * 18 * sizeof(double) + 256);
+  tq_status st = ensure(s, s->red, kRedBytes);
   if (st != TQ_OK) return st;
   if ((st = ensure_pinned(s, s->pin_small, 4096)) != TQ_OK) return st;
   char* d = static_cast<char*>(s->red.ptr);
@@ -311,12 +440,10 @@ tq_status reduce_impl(tq_state* s, const unsigned long long* masks, int n_masks,
     std::memcpy(hm, masks, n_masks * sizeof(unsigned long long));
     e = cudaMemcpyAsync(d + kRedMasks, hm, n_masks * sizeof(unsigned long long), cudaMemcpyHostToDevice, s->stream);
   }
-  if (e == cudaSuccess)
-    e = launch_diag_reduce(s->rho, s->n, s->prec, reinterpret_cast<unsigned long long*>(d + kRedMasks), n_masks,
-                           reinterpret_cast<double*>(d + kRedPartials), reinterpret_cast<double*>(d + kRedOut),
-                           normalize, s->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hout, d + kRedOut, (2 + n_masks) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  st = reduce_device(s, reinterpret_cast<unsigned long long*>(d + kRedMasks), n_masks, normalize, nullptr);
+  if (st != TQ_OK) return st;
+  e = cudaMemcpyAsync(hout, d + kRedOut, (2 + n_masks) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e);
   std::memcpy(host_out, hout, (2 + n_masks) * sizeof(double));
@@ -341,11 +468,17 @@ void tq_free(tq_state* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
   if (s->owns_rho && s->rho) cudaFree(s->rho);
-  for (DevBuf* b : {&s->upload, &s->sops, &s->sb64, &s->sb32, &s->red, &s->probs, &s->staging})
-    if (b->ptr) cudaFree(b->ptr);
+  for (DevBuf* b : {&s->red, &s->probs, &s->staging, &s->scratch.blob, &s->scratch.sops, &s->scratch.sb64,
+                    &s->scratch.sb32})
+    free_buf(*b);
   for (PinBuf* b : {&s->pin, &s->pin_small})
     if (b->ptr) cudaFreeHost(b->ptr);
   if (s->pin_free) cudaEventDestroy(s->pin_free);
+  for (const Pending& pd : s->pending) {
+    cudaEventDestroy(pd.e0);
+    cudaEventDestroy(pd.e1);
+  }
+  for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
   delete s;
 }
 
@@ -359,6 +492,7 @@ tq_status tq_info(const tq_state* s, int* n_qubits, int* precision) {
 tq_status tq_reset(tq_state* s) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
+  s->launches += 1;
   return cuda_fail(s, launch_init_zero_state(s->rho, s->n, s->prec, s->stream));
 }
 
@@ -385,6 +519,7 @@ tq_status tq_get_rho(tq_state* s, double* out) {
     const size_t cnt = std::min(chunk, entries - c0);
     e = launch_convert_f32_to_f64(static_cast<const float*>(s->rho) + 2 * c0, static_cast<double*>(s->staging.ptr),
                                   2 * cnt, s->stream);
+    s->launches += 1;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out + 2 * c0, s->staging.ptr, cnt * 16, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -412,6 +547,7 @@ tq_status tq_set_rho(tq_state* s, const double* in) {
     if (e == cudaSuccess)
       e = launch_convert_f64_to_f32(static_cast<const double*>(s->staging.ptr), static_cast<float*>(s->rho) + 2 * c0,
                                     2 * cnt, s->stream);
+    s->launches += 1;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e);
   }
@@ -444,6 +580,64 @@ tq_status tq_run_circuit(tq_state* s, const tq_op* ops, size_t n_ops, int max_fu
   return run_impl(s, ops, n_ops, max_fuse_width, n_blocks_out);
 }
 
+tq_status tq_program_create(int n, int precision, const tq_op* ops, size_t n_ops, int max_fuse_width,
+                            tq_program** out) {
+  if (!out) return TQ_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits || (precision != TQ_FP64 && precision != TQ_SPLIT) || (!ops && n_ops))
+    return TQ_ERR_ARG;
+  tq_program* P = new (std::nothrow) tq_program();
+  if (!P) return TQ_ERR_OOM;
+  HostTables t;
+  tq_status st = plan_program(n, precision, ops, n_ops, max_fuse_width, P, &t);
+  if (st != TQ_OK) {
+    delete P;
+    return st;
+  }
+  cudaError_t e = grow(P->blob, P->blob_bytes, nullptr, false);
+  if (e == cudaSuccess) e = grow(P->sops, t.sop_entries * sizeof(double2) + 16, nullptr, false);
+  if (e == cudaSuccess) e = grow(P->sb64, t.sb_entries * sizeof(double2) + 16, nullptr, false);
+  if (e == cudaSuccess && precision == TQ_SPLIT) e = grow(P->sb32, t.sb_entries * sizeof(float2) + 16, nullptr, false);
+  if (e == cudaSuccess) {
+    std::vector<char> h(P->blob_bytes);
+    pack_blob(*P, t, h.data());
+    e = cudaMemcpy(P->blob.ptr, h.data(), P->blob_bytes, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    tq_program_free(P);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return TQ_ERR_OOM;
+    }
+    return TQ_ERR_CUDA;
+  }
+  *out = P;
+  return TQ_OK;
+}
+
+tq_status tq_program_run(tq_state* s, const tq_program* p) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (!p || p->n != s->n || p->prec != s->prec) return TQ_ERR_ARG;
+  return enqueue_program(s, *p);
+}
+
+tq_status tq_program_info(const tq_program* p, size_t* n_ops, size_t* n_blocks, int* max_width,
+                          size_t* table_bytes) {
+  if (!p) return TQ_ERR_ARG;
+  if (table_bytes) *table_bytes = p->blob_bytes;
+  if (n_ops) *n_ops = p->n_ops;
+  if (n_blocks) *n_blocks = p->params.size();
+  if (max_width) *max_width = p->max_width;
+  return TQ_OK;
+}
+
+void tq_program_free(tq_program* p) {
+  if (!p) return;
+  for (DevBuf* b : {&p->blob, &p->sops, &p->sb64, &p->sb32}) free_buf(*b);
+  delete p;
+}
+
 tq_status tq_trace(tq_state* s, double* re, double* im) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
@@ -468,6 +662,13 @@ tq_status tq_expect_z(tq_state* s, const uint64_t* masks, int n_masks, double* o
   return TQ_OK;
 }
 
+tq_status tq_expect_z_device(tq_state* s, const uint64_t* masks_dev, int n_masks, double* out_dev) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (n_masks < 1 || n_masks > 16 || !masks_dev || !out_dev) return TQ_ERR_ARG;
+  return reduce_device(s, reinterpret_cast<const unsigned long long*>(masks_dev), n_masks, s->prec == TQ_SPLIT, out_dev);
+}
+
 tq_status tq_probs(tq_state* s, double* out) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
@@ -481,9 +682,53 @@ tq_status tq_probs(tq_state* s, double* out) {
     tr = reinterpret_cast<const double*>(static_cast<char*>(s->red.ptr) + kRedOut);
   }
   cudaError_t e = launch_diag_probs(s->rho, s->n, s->prec, tr, static_cast<double*>(s->probs.ptr), s->stream);
+  s->launches += 1;
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->probs.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_fail(s, e);
+}
+
+tq_status tq_profile_enable(tq_state* s, int on) {
+  if (!s) return TQ_ERR_ARG;
+  if (on) {
+    cudaStreamSynchronize(s->stream);
+    fold_pending(s);
+    for (int k = 0; k < K_NKINDS; ++k) {
+      s->prof_launches[k] = 0;
+      s->prof_ms[k] = s->prof_flops[k] = s->prof_bytes[k] = 0.0;
+    }
+  }
+  s->prof_on = on != 0;
+  return TQ_OK;
+}
+
+tq_status tq_profile_read(tq_state* s, tq_kernel_stat* out, int capacity, int* count) {
+  if (!s || !count || (capacity > 0 && !out)) return TQ_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  fold_pending(s);
+  int c = 0;
+  for (int k = 0; k < K_NKINDS; ++k) {
+    if (!s->prof_launches[k]) continue;
+    if (c < capacity) {
+      tq_kernel_stat& o = out[c];
+      std::memset(&o, 0, sizeof(o));
+      std::strncpy(o.name, kKindName[k], sizeof(o.name) - 1);
+      o.launches = s->prof_launches[k];
+      o.total_ms = s->prof_ms[k];
+      o.flops = s->prof_flops[k];
+      o.bytes = s->prof_bytes[k];
+    }
+    ++c;
+  }
+  *count = c;
+  return TQ_OK;
+}
+
+tq_status tq_launch_count(const tq_state* s, uint64_t* out) {
+  if (!s || !out) return TQ_ERR_ARG;
+  *out = s->launches;
+  return TQ_OK;
 }
 
 }  // extern "C"

@@ -264,3 +264,45 @@ def test_full_size_15q_factorised_fp64(tq):
 
 def test_full_size_15q_factorised_split(tq):
     _factorised_check(tq, 15, [1, 7, 12, 14], -1, "split", 30, 16, tol=2e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_device_program_equals_host_call(tq, precision):
+    import torch
+    n = 9
+    c = W.tfim_ring(n, steps=1)
+    prog = tq.DeviceProgram(n, c.ops, width=-1, precision=precision)
+    assert prog.n_ops == len(c.ops) and prog.n_blocks >= 1 and prog.table_bytes > 0
+    masks = torch.tensor([0b11, 1 << 8], dtype=torch.int64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    with tq.State(n, precision) as a, tq.State(n, precision) as b:
+        for _ in range(3):
+            a.run_program(prog)
+            b.run(c.ops, width=-1)
+        a.expect_z_device(masks.data_ptr(), 2, out.data_ptr())
+        va, vb = a.vec(), b.vec()
+        zb = b.expect_z([0b11, 1 << 8])
+    assert np.array_equal(va, vb)                  # same kernels, same order: bitwise equal
+    assert np.array_equal(out.cpu().numpy(), zb)
+    prog.free()
+    with pytest.raises(tq.TqError):
+        with tq.State(n - 1, precision) as st:
+            st.run_program(tq.DeviceProgram(n, c.ops, precision=precision))
+
+
+def test_profile_counts_launches(tq):
+    n = 8
+    c = W.tfim_ring(n, steps=2)
+    with tq.State(n, "fp64") as st:
+        st.profile(True)
+        l0 = st.launch_count()
+        nb = st.run(c.ops, width=2)
+        st.expect_z([3])
+        stats = st.profile_stats()
+        assert st.launch_count() - l0 == 1 + 1 + nb + 2
+    assert stats["apply_f64_w2"]["launches"] == nb
+    assert stats["superop_build"]["launches"] == 1 and stats["fuse"]["launches"] == 1
+    assert stats["reduce"]["launches"] == 2
+    assert stats["apply_f64_w2"]["flops"] == 8.0 * 4 ** n * 16
+    assert stats["apply_f64_w2"]["bytes"] == 2 * 16 * 4 ** n
+    assert all(v["total_ms"] > 0 for v in stats.values())
