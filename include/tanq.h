@@ -221,6 +221,35 @@ void tq_program_free(tq_program* p);
  * device pointers. Asynchronous on the state's stream. */
 tq_status tq_expect_z_device(tq_state* s, const uint64_t* masks_dev, int n_masks, double* out_dev);
 
+/* ---- allocation-free readout ---------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not let the library allocate device memory: a host program whose
+ * HBM is entirely owned by another allocator (such as PyTorch's caching
+ * allocator in a serving process), or one that cannot afford the device-wide
+ * synchronisation that cudaFree implies.
+ *
+ * Same result as tq_expect_z_device, but for a caller-owned vec(rho) (no
+ * tq_state): out_dev[i] = Re Tr(rho Z_{masks_dev[i]}) for i < n_masks, divided
+ * by Re Tr(rho) when precision is TQ_SPLIT. rho_dev holds 4^n_qubits complex
+ * entries (complex128 for TQ_FP64, complex64 for TQ_SPLIT) in vec order;
+ * masks_dev and out_dev are device arrays of n_masks entries. Enqueued on
+ * cuda_stream; returns without waiting.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (at most 152 x 18 partial sums plus the totals, 22,144 bytes) is a fixed
+ * device array inside the library, present on every GPU that loads the
+ * library until the process exits. Limits: 1 <= n_masks <= 16 and
+ * 1 <= n_qubits <= 16; larger requests return TQ_ERR_ARG. The first call on
+ * each device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the one
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads without ordering) race and give wrong results;
+ * order them on one stream. Nothing in the array needs clearing between
+ * calls: each call writes every partial it later reads. */
+tq_status tq_expect_z_noalloc(const void* rho_dev, int n_qubits, int precision,
+                              const uint64_t* masks_dev, int n_masks, double* out_dev,
+                              void* cuda_stream);
+
 /* ---- per-launch profiling (CUDA events on the state's stream) ---------- */
 
 typedef struct tq_kernel_stat {

@@ -69,6 +69,7 @@ _SIGNATURES = [
     ("tq_program_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int), POINTER(c_size_t)]),
     ("tq_program_free", None, [c_void_p]),
     ("tq_expect_z_device", c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    ("tq_expect_z_noalloc", c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     ("tq_profile_enable", c_int, [c_void_p, c_int]),
     ("tq_profile_read", c_int, [c_void_p, POINTER(TqKernelStat), c_int, POINTER(c_int)]),
     ("tq_launch_count", c_int, [c_void_p, POINTER(c_uint64)]),
@@ -204,6 +205,15 @@ def channel_kraus(name: str, k: int, params) -> list[np.ndarray]:
     _check(lib.tq_channel_kraus(CHANNELS[name], k, _dptr(p), m.value, ctypes.byref(m), _dptr(out)), "tq_channel_kraus")
     arr = out.view(np.complex128).reshape(m.value, d, d)
     return [arr[i] for i in range(m.value)]
+
+
+def expect_z_noalloc(rho_dev_ptr: int, n: int, precision: str, masks_dev_ptr: int, n_masks: int,
+                     out_dev_ptr: int, stream=None):
+    """Allocation-free <Z> readout on caller-owned device buffers (see
+    tq_expect_z_noalloc in include/tanq.h)."""
+    lib = load()
+    _check(lib.tq_expect_z_noalloc(c_void_p(rho_dev_ptr), n, PRECISION[precision], c_void_p(masks_dev_ptr), n_masks,
+                                   c_void_p(out_dev_ptr), c_void_p(stream)), "tq_expect_z_noalloc")
 
 
 def group_base(g: int, positions) -> int:
