@@ -221,6 +221,100 @@ void tq_program_free(tq_program* p);
  * device pointers. Asynchronous on the state's stream. */
 tq_status tq_expect_z_device(tq_state* s, const uint64_t* masks_dev, int n_masks, double* out_dev);
 
+/* ---- batched execution (many independent circuits, one persistent launch) --
+ * Jobs are independent circuits, each on its own |0..0><0..0| state of n
+ * qubits (1..16) of the batch's precision. tq_batch_run resets every state,
+ * builds and fuses all superoperators (two launches over all jobs), applies
+ * every job's fused blocks in ONE persistent kernel launch, and reduces each
+ * job's trace and <Z_mask> values; the sequence is captured as a CUDA graph
+ * on the first run (on a private stream) and replayed by later runs on the
+ * batch's stream. Small registers (vec(rho) <= 64 KiB) run their whole
+ * circuit in shared memory; larger ones are split into tiles whose order
+ * respects each job's block sequence (single-kernel execution, Sec. 3.4 and
+ * Listing 2, applied across independent circuits). */
+
+typedef struct tq_batch tq_batch;
+
+/* An empty batch working on `cuda_stream` (NULL: legacy default stream). */
+tq_status tq_batch_create(int precision, void* cuda_stream, tq_batch** out);
+
+/* Add a job: ops as in tq_run_circuit, fused with max_fuse_width in
+ * {-1, 0, 1, 2} (-1: cost model, capped at 2; 3 and 4 give
+ * TQ_ERR_UNSUPPORTED, as does any op on more than 2 qubits); masks: up to 16
+ * Z-masks to read out after the run. *job_out receives the job index. */
+tq_status tq_batch_add(tq_batch* b, int n_qubits, const tq_op* ops, size_t n_ops, int max_fuse_width,
+                       const uint64_t* masks, int n_masks, int* job_out);
+
+/* Entries per tile (2^tile_log2) for the jobs of n_qubits qubits: the work
+ * granularity of the persistent kernel, normally set by the autotuner. */
+tq_status tq_batch_set_tile(tq_batch* b, int n_qubits, int tile_log2);
+
+/* Enqueue one run of every job (asynchronous). */
+tq_status tq_batch_run(tq_batch* b);
+
+/* Failure-detection hook for tests: every device-side wait of the batch
+ * kernel gives up after max_spin polls (default 2e7, seconds), sets an error
+ * flag and lets the kernel finish; with never_ready_job >= 0 that job's waits
+ * can never be satisfied, so a run ends with TQ_ERR_TIMEOUT from
+ * tq_batch_wait while the CUDA context stays usable. -1 restores normal
+ * waits. */
+tq_status tq_batch_test_wait_limit(tq_batch* b, long long max_spin, int never_ready_job);
+
+/* Wait for the last run; TQ_ERR_TIMEOUT if a bounded device-side wait ran
+ * out (the results are then invalid). */
+tq_status tq_batch_wait(tq_batch* b);
+
+/* out[0..1] = Re, Im Tr(rho_job); out[2+i] = Re Tr(rho_job Z_{mask_i}) (divided
+ * by Re Tr rho_job in TQ_SPLIT). Waits for the run. */
+tq_status tq_batch_result(tq_batch* b, int job, double* out);
+
+/* vec(rho_job) as 2*4^n interleaved doubles (waits for the run). */
+tq_status tq_batch_get_rho(tq_batch* b, int job, double* out);
+
+/* Jobs, work items of the persistent launch, bytes of all density matrices. */
+tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size_t* rho_bytes);
+
+void tq_batch_free(tq_batch* b);
+
+/* ---- serving loop (continuous batching of circuit requests) --------------
+ * Requests (independent circuits, each on its own |0..0><0..0|) wait in a
+ * FIFO queue. A request is admitted, in order, when its density matrix fits
+ * the rho budget (16*4^n bytes FP64, 8*4^n split; memory from a device arena
+ * allocated once at creation) and a live slot is free; admission uploads its
+ * tables and builds and fuses its superoperators (FP64, GPU). Each
+ * tq_server_step is one tick: admit, then ONE persistent batch-kernel launch
+ * that advances every live request by a quantum of fused blocks (about eight
+ * 12-qubit passes' worth of entries, at least one block), then readouts of
+ * the requests that finished, whose memory is returned. rho stays resident
+ * between ticks; requests submitted while others run join the next tick. */
+
+typedef struct tq_server tq_server;
+
+/* rho_budget_bytes: device memory for the live density matrices;
+ * table_budget_bytes: for their Kraus sets, plans and superoperators;
+ * max_live: live requests at most. Allocates both budgets up front. */
+tq_status tq_server_create(int precision, void* cuda_stream, size_t rho_budget_bytes,
+                           size_t table_budget_bytes, int max_live, tq_server** out);
+
+/* Queue a request (ops and masks as in tq_batch_add; widths <= 2).
+ * TQ_ERR_OOM if its density matrix can never fit the budget. */
+tq_status tq_server_submit(tq_server* s, int n_qubits, const tq_op* ops, size_t n_ops,
+                           int max_fuse_width, const uint64_t* masks, int n_masks, int* request_id);
+
+/* One tick (waits for it). Outputs (may be NULL): live requests, queued
+ * requests, requests finished in this tick. */
+tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finished);
+
+/* *state: 0 queued, 1 live, 2 done; when done, out (if not NULL) receives
+ * 2 + n_masks doubles as in tq_batch_result. */
+tq_status tq_server_poll(tq_server* s, int request_id, int* state, double* out);
+
+/* Bytes of live density matrices, ticks run, fused blocks applied. */
+tq_status tq_server_info(const tq_server* s, size_t* rho_live_bytes, unsigned long long* ticks,
+                         unsigned long long* blocks_applied);
+
+void tq_server_free(tq_server* s);
+
 /* ---- allocation-free readout ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not let the library allocate device memory: a host program whose

@@ -69,6 +69,25 @@ _SIGNATURES = [
     ("tq_program_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int), POINTER(c_size_t)]),
     ("tq_program_free", None, [c_void_p]),
     ("tq_expect_z_device", c_int, [c_void_p, c_void_p, c_int, c_void_p]),
+    ("tq_batch_create", c_int, [c_int, c_void_p, POINTER(c_void_p)]),
+    ("tq_batch_add", c_int, [c_void_p, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_uint64), c_int,
+                             POINTER(c_int)]),
+    ("tq_batch_set_tile", c_int, [c_void_p, c_int, c_int]),
+    ("tq_batch_run", c_int, [c_void_p]),
+    ("tq_batch_test_wait_limit", c_int, [c_void_p, ctypes.c_longlong, c_int]),
+    ("tq_batch_wait", c_int, [c_void_p]),
+    ("tq_batch_result", c_int, [c_void_p, c_int, POINTER(c_double)]),
+    ("tq_batch_get_rho", c_int, [c_void_p, c_int, POINTER(c_double)]),
+    ("tq_batch_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_size_t)]),
+    ("tq_batch_free", None, [c_void_p]),
+    ("tq_server_create", c_int, [c_int, c_void_p, c_size_t, c_size_t, c_int, POINTER(c_void_p)]),
+    ("tq_server_submit", c_int, [c_void_p, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_uint64), c_int,
+                                 POINTER(c_int)]),
+    ("tq_server_step", c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    ("tq_server_poll", c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
+    ("tq_server_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(ctypes.c_ulonglong),
+                               POINTER(ctypes.c_ulonglong)]),
+    ("tq_server_free", None, [c_void_p]),
     ("tq_expect_z_noalloc", c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     ("tq_profile_enable", c_int, [c_void_p, c_int]),
     ("tq_profile_read", c_int, [c_void_p, POINTER(TqKernelStat), c_int, POINTER(c_int)]),
@@ -162,6 +181,123 @@ class DeviceProgram:
     def free(self):
         if self._h:
             _lib.tq_program_free(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent circuits run in one persistent launch (tq_batch)."""
+
+    def __init__(self, precision: str = "fp64", stream=None):
+        lib = load()
+        self.precision = precision
+        torch = _torch_plumbing()
+        if stream is None and torch is not None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = c_void_p()
+        self._nmasks = []
+        self._n = []
+        _check(lib.tq_batch_create(PRECISION[precision], c_void_p(stream), ctypes.byref(self._h)), "tq_batch_create")
+
+    def add(self, n: int, ops, width: int = -1, masks=()) -> int:
+        prog = ops if isinstance(ops, Program) else Program(ops)
+        m = (c_uint64 * max(1, len(masks)))(*[int(v) for v in masks])
+        j = c_int(0)
+        _check(_lib.tq_batch_add(self._h, n, prog.arr, prog.n_ops, width, m, len(masks), ctypes.byref(j)),
+               "tq_batch_add")
+        self._nmasks.append(len(masks))
+        self._n.append(n)
+        return j.value
+
+    def set_tile(self, n: int, tile_log2: int):
+        _check(_lib.tq_batch_set_tile(self._h, n, tile_log2), "tq_batch_set_tile")
+
+    def run(self):
+        _check(_lib.tq_batch_run(self._h), "tq_batch_run")
+
+    def test_wait_limit(self, max_spin: int, never_ready_job: int = -1):
+        _check(_lib.tq_batch_test_wait_limit(self._h, max_spin, never_ready_job), "tq_batch_test_wait_limit")
+
+    def wait(self):
+        _check(_lib.tq_batch_wait(self._h), "tq_batch_wait")
+
+    def result(self, job: int) -> np.ndarray:
+        out = np.zeros(2 + self._nmasks[job])
+        _check(_lib.tq_batch_result(self._h, job, _dptr(out)), "tq_batch_result")
+        return out
+
+    def rho(self, job: int) -> np.ndarray:
+        n = self._n[job]
+        N = 1 << n
+        out = np.zeros(2 << (2 * n))
+        _check(_lib.tq_batch_get_rho(self._h, job, _dptr(out)), "tq_batch_get_rho")
+        return out.view(np.complex128).reshape(N, N).T.copy()
+
+    def info(self):
+        a, b, c = c_size_t(0), c_size_t(0), c_size_t(0)
+        _check(_lib.tq_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tq_batch_info")
+        return {"jobs": a.value, "items": b.value, "rho_bytes": c.value}
+
+    def free(self):
+        if self._h:
+            _lib.tq_batch_free(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching serving loop (tq_server)."""
+
+    def __init__(self, precision: str = "fp64", rho_budget: int = 1 << 30, table_budget: int = 1 << 28,
+                 max_live: int = 64, stream=None):
+        lib = load()
+        self.precision = precision
+        torch = _torch_plumbing()
+        if stream is None and torch is not None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = c_void_p()
+        self._nmasks = {}
+        _check(lib.tq_server_create(PRECISION[precision], c_void_p(stream), rho_budget, table_budget, max_live,
+                                    ctypes.byref(self._h)), "tq_server_create")
+
+    def submit(self, n: int, ops, width: int = -1, masks=()) -> int:
+        prog = ops if isinstance(ops, Program) else Program(ops)
+        m = (c_uint64 * max(1, len(masks)))(*[int(v) for v in masks])
+        rid = c_int(0)
+        _check(_lib.tq_server_submit(self._h, n, prog.arr, prog.n_ops, width, m, len(masks), ctypes.byref(rid)),
+               "tq_server_submit")
+        self._nmasks[rid.value] = len(masks)
+        return rid.value
+
+    def step(self):
+        a, b, c = c_int(0), c_int(0), c_int(0)
+        _check(_lib.tq_server_step(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tq_server_step")
+        return a.value, b.value, c.value
+
+    def poll(self, rid: int):
+        st = c_int(0)
+        out = np.zeros(2 + self._nmasks[rid])
+        _check(_lib.tq_server_poll(self._h, rid, ctypes.byref(st), _dptr(out)), "tq_server_poll")
+        return st.value, (out if st.value == 2 else None)
+
+    def info(self):
+        a, b, c = c_size_t(0), ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+        _check(_lib.tq_server_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tq_server_info")
+        return {"rho_live_bytes": a.value, "ticks": b.value, "blocks_applied": c.value}
+
+    def free(self):
+        if self._h:
+            _lib.tq_server_free(self._h)
             self._h = c_void_p()
 
     def __del__(self):

@@ -1,0 +1,245 @@
+// Device side of batched execution, shared by the batch engine (tq_batch.cu)
+// and the serving loop (tq_serve.cu).
+//
+// Work is a list of items in a fixed global order; CTAs take items from a
+// ticket counter. An item is either a run of consecutive fused blocks of a
+// job whose vec(rho) fits in shared memory ("resident": load rho once, apply
+// the blocks with block-wide barriers between them, store once) or a range
+// of tiles of one fused block of a larger job. A tile item of block b waits
+// until the job's tile counter shows every tile of block b-1 finished.
+// Items are ordered round-robin over jobs by block index, so an item only
+// ever waits for items with smaller tickets, which are already held by
+// running CTAs: the waits always end. Each wait is still bounded; when the
+// bound runs out the kernel raises an error flag, skips the remaining work
+// and returns, and the host reports TQ_ERR_TIMEOUT.
+#pragma once
+
+#include "tq_plan.cuh"
+
+namespace tq {
+namespace batch {
+
+constexpr int kThreads = 256;
+constexpr int kResidentBytes = 64 * 1024;  // vec(rho) of a resident job
+constexpr int kSEntries = 256;             // superoperator cache: widths <= 2
+constexpr int kMaxMasks = 16;
+constexpr int kResults = 2 + kMaxMasks;    // Re tr, Im tr, masked sums
+
+struct BJob {
+  unsigned long long rho_off;  // byte offset of vec(rho) in the arena
+  int n;
+  int n_blocks;
+  int block0;     // first block in the block table
+  int tile_log2;  // entries per tile (tile jobs)
+  int resident;
+  int n_masks;
+  int never_ready;  // test hook: this job's waits can never be satisfied
+  int pad;
+  unsigned long long masks[kMaxMasks];
+};
+
+struct BBlk {
+  ApplyParams p;
+  const void* S;  // fused superoperator, 4^w x 4^w row-major (double2 or float2)
+};
+
+struct BItem {
+  int job;
+  int block;   // tile item: block index (job-relative); -1: resident item
+  int tile0;   // tile item: first tile; resident item: first block
+  int ntiles;  // tile item: tiles; resident item: blocks
+};
+
+template <typename T2>
+struct Cx;
+template <>
+struct Cx<double2> {
+  __device__ __forceinline__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ __forceinline__ static void fma(double2& acc, double2 a, double2 b) {
+    acc.x = ::fma(a.x, b.x, acc.x);
+    acc.x = ::fma(-a.y, b.y, acc.x);
+    acc.y = ::fma(a.x, b.y, acc.y);
+    acc.y = ::fma(a.y, b.x, acc.y);
+  }
+  __device__ __forceinline__ static double2 ldcg(const double2* p) { return __ldcg(p); }
+};
+template <>
+struct Cx<float2> {
+  __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+  __device__ __forceinline__ static void fma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+  }
+  __device__ __forceinline__ static float2 ldcg(const float2* p) { return __ldcg(p); }
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// One group of a width-K block: gather its 4^K entries, multiply by S
+// (shared memory), scatter back. GLOBAL: rho in global memory, loaded
+// through L2 only (other CTAs wrote it); else rho is the shared-memory copy.
+template <typename T2, int K, bool GLOBAL>
+__device__ __forceinline__ void apply_group(T2* rho, unsigned long long g, const ApplyParams& p, const T2* sS) {
+  constexpr int D = 1 << (2 * K);
+  unsigned long long base = g;
+#pragma unroll
+  for (int i = 0; i < 2 * K; ++i) {
+    const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
+    base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
+  }
+  T2 x[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) x[l] = GLOBAL ? Cx<T2>::ldcg(&rho[base + p.off[l]]) : rho[base + p.off[l]];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    T2 acc = Cx<T2>::zero();
+#pragma unroll
+    for (int j = 0; j < D; ++j) Cx<T2>::fma(acc, sS[i * D + j], x[j]);
+    rho[base + p.off[i]] = acc;
+  }
+}
+
+template <typename T2>
+__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS) {
+  if (threadIdx.x == 0) *s_blk = *blk;
+  __syncthreads();
+  const int D = 1 << (2 * s_blk->p.width);
+  const T2* S = static_cast<const T2*>(s_blk->S);
+  for (int e = threadIdx.x; e < D * D; e += blockDim.x) sS[e] = S[e];
+  __syncthreads();
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(kThreads) k_batch_apply(char* arena, const BJob* __restrict__ jobs,
+                                                          const BBlk* __restrict__ blks,
+                                                          const BItem* __restrict__ items, int n_items,
+                                                          int* counters, int* ticket, int* err, long long max_spin) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T2* sS = reinterpret_cast<T2*>(smem);
+  T2* sR = sS + kSEntries;
+  __shared__ BBlk s_blk;
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= n_items) break;
+    const BItem it = items[idx];
+    const BJob& jb = jobs[it.job];
+    T2* rho = reinterpret_cast<T2*>(arena + jb.rho_off);
+    const int n = jb.n;
+    if (it.block < 0) {
+      // resident job: the whole circuit on a shared-memory copy of rho
+      const int N = 1 << (2 * n);
+      for (int e = threadIdx.x; e < N; e += blockDim.x) sR[e] = Cx<T2>::ldcg(&rho[e]);
+      for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
+        stage_block(&blks[jb.block0 + b], &s_blk, sS);
+        const ApplyParams& p = s_blk.p;
+        for (unsigned long long g = threadIdx.x; g < p.n_groups; g += blockDim.x) {
+          if (p.width == 1)
+            apply_group<T2, 1, false>(sR, g, p, sS);
+          else
+            apply_group<T2, 2, false>(sR, g, p, sS);
+        }
+        __syncthreads();
+      }
+      for (int e = threadIdx.x; e < N; e += blockDim.x) rho[e] = sR[e];
+      __syncthreads();
+      continue;
+    }
+    // tile item: wait until every tile of the previous block of this job is done
+    if (threadIdx.x == 0 && it.block > 0) {
+      const int need = jb.never_ready ? 0x7fffffff : it.block << (2 * n - jb.tile_log2);
+      long long spins = 0;
+      while (ld_acquire(&counters[it.job]) < need) {
+        if (ld_acquire(err) != 0) break;
+        if (++spins > max_spin) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS);
+    const ApplyParams& p = s_blk.p;
+    if (*(volatile int*)err == 0) {
+      const unsigned long long gpt = 1ull << (jb.tile_log2 - 2 * p.width);  // groups per tile
+      const unsigned long long g0 = (unsigned long long)it.tile0 * gpt;
+      const unsigned long long g1 = min(p.n_groups, g0 + (unsigned long long)it.ntiles * gpt);
+      for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        if (p.width == 1)
+          apply_group<T2, 1, true>(rho, g, p, sS);
+        else
+          apply_group<T2, 2, true>(rho, g, p, sS);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&counters[it.job], it.ntiles);
+    }
+  }
+}
+
+static __global__ void k_batch_set_one(char* arena, const BJob* __restrict__ jobs, int n_jobs, int precision) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_jobs) return;
+  if (precision == 0)
+    reinterpret_cast<double2*>(arena + jobs[j].rho_off)[0] = make_double2(1.0, 0.0);
+  else
+    reinterpret_cast<float2*>(arena + jobs[j].rho_off)[0] = make_float2(1.f, 0.f);
+}
+
+// Per-job FP64 readouts: one CTA per job, fixed thread mapping and tree.
+template <typename T2>
+__global__ void __launch_bounds__(kThreads) k_batch_reduce(const char* arena, const BJob* __restrict__ jobs,
+                                                           int normalize, double* __restrict__ out) {
+  __shared__ double red[kResults][kThreads];
+  const BJob& jb = jobs[blockIdx.x];
+  const T2* rho = reinterpret_cast<const T2*>(arena + jb.rho_off);
+  const unsigned long long N = 1ull << jb.n;
+  double acc[kResults];
+#pragma unroll
+  for (int q = 0; q < kResults; ++q) acc[q] = 0.0;
+  for (unsigned long long x = threadIdx.x; x < N; x += kThreads) {
+    const T2 v = rho[x * (N + 1)];
+    const double re = (double)v.x;
+    acc[0] += re;
+    acc[1] += (double)v.y;
+#pragma unroll
+    for (int q = 0; q < kMaxMasks; ++q)
+      if (q < jb.n_masks) acc[2 + q] += (__popcll(x & jb.masks[q]) & 1) ? -re : re;
+  }
+#pragma unroll
+  for (int q = 0; q < kResults; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int q = 0; q < kResults; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < kResults) {
+    double v = red[threadIdx.x][0];
+    if (normalize && threadIdx.x >= 2) v /= red[0][0];
+    out[blockIdx.x * kResults + threadIdx.x] = v;
+  }
+}
+
+template <typename T2>
+inline size_t apply_smem() {
+  return kSEntries * sizeof(T2) + kResidentBytes;
+}
+
+inline bool is_resident(int n, int prec) {
+  return (size_t)(prec == 0 ? 16 : 8) << (2 * n) <= (size_t)kResidentBytes;
+}
+
+}  // namespace batch
+}  // namespace tq

@@ -1,0 +1,65 @@
+// Planning structures shared by the single-state path and the batch engine
+// (CUDA translation units only).
+#pragma once
+
+#include <vector>
+
+#include "tq_device.cuh"
+#include "tq_internal.h"
+
+namespace tq {
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t cap = 0;
+};
+
+struct PinBuf {
+  void* ptr = nullptr;
+  size_t cap = 0;
+};
+
+
+// Host tables of one planned circuit, packed into a single upload.
+struct HostTables {
+  std::vector<double2> kraus;
+  std::vector<OpDesc> ops;
+  std::vector<BlockDesc> blocks;
+  std::vector<MemberDesc> members;
+  std::vector<FuseWork> work;
+  long long sop_entries = 0;
+  long long sb_entries = 0;
+};
+
+
+}  // namespace tq
+
+// A planned circuit: host-side launch parameters plus device tables.
+struct tq_program {
+  int n = 0;
+  int prec = 0;
+  size_t n_ops = 0;
+  int max_width = 0;
+  int max_dim2 = 0;
+  int n_work = 0;
+  std::vector<tq::ApplyParams> params;  // per block
+  std::vector<long long> sb_off;    // per block, complex entries
+  // device tables (one blob: Kraus sets, op/block/member/work tables)
+  tq::DevBuf blob, sops, sb64, sb32;
+  size_t o_kraus = 0, o_ops = 0, o_blk = 0, o_mem = 0, o_work = 0, blob_bytes = 0;
+  bool owns = true;  // standalone programs own their buffers
+};
+
+
+namespace tq {
+
+ApplyParams apply_params(int n, const Block& B);
+
+// Validate, resolve and plan `ops` into P's host fields and `t`.
+tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t);
+
+void pack_blob(const tq_program& P, const HostTables& t, char* h);
+
+}  // namespace tq

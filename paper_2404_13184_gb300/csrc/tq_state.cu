@@ -9,22 +9,12 @@
 
 #include "tq_device.cuh"
 #include "tq_internal.h"
+#include "tq_plan.cuh"
 
 using namespace tq;
 
 namespace {
 
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-struct DevBuf {
-  void* ptr = nullptr;
-  size_t cap = 0;
-};
-
-struct PinBuf {
-  void* ptr = nullptr;
-  size_t cap = 0;
-};
 
 // Kernel kinds for launch counting and event profiling.
 enum Kind { K_BUILD = 0, K_FUSE, K_REDUCE, K_APPLY64 /* +w-1 */, K_APPLY32 = K_APPLY64 + 4, K_NKINDS = K_APPLY32 + 4 };
@@ -38,22 +28,6 @@ struct Pending {
 };
 
 }  // namespace
-
-// A planned circuit: host-side launch parameters plus device tables.
-struct tq_program {
-  int n = 0;
-  int prec = 0;
-  size_t n_ops = 0;
-  int max_width = 0;
-  int max_dim2 = 0;
-  int n_work = 0;
-  std::vector<ApplyParams> params;  // per block
-  std::vector<long long> sb_off;    // per block, complex entries
-  // device tables (one blob: Kraus sets, op/block/member/work tables)
-  DevBuf blob, sops, sb64, sb32;
-  size_t o_kraus = 0, o_ops = 0, o_blk = 0, o_mem = 0, o_work = 0, blob_bytes = 0;
-  bool owns = true;  // standalone programs own their buffers
-};
 
 struct tq_state {
   int n = 0;
@@ -183,15 +157,9 @@ void fold_pending(tq_state* s) {
 
 // ---- planning ------------------------------------------------------------
 
-struct HostTables {
-  std::vector<double2> kraus;
-  std::vector<OpDesc> ops;
-  std::vector<BlockDesc> blocks;
-  std::vector<MemberDesc> members;
-  std::vector<FuseWork> work;
-  long long sop_entries = 0;
-  long long sb_entries = 0;
-};
+}  // namespace
+
+namespace tq {
 
 ApplyParams apply_params(int n, const Block& B) {
   ApplyParams p{};
@@ -295,6 +263,10 @@ void pack_blob(const tq_program& P, const HostTables& t, char* h) {
   std::memcpy(h + P.o_mem, t.members.data(), t.members.size() * sizeof(MemberDesc));
   std::memcpy(h + P.o_work, t.work.data(), t.work.size() * sizeof(FuseWork));
 }
+
+}  // namespace tq
+
+namespace {
 
 // Enqueue superoperator build, fusion and every apply pass of P on s.
 tq_status enqueue_program(tq_state* s, const tq_program& P) {

@@ -1,0 +1,126 @@
+"""Batched execution (tq_batch): many independent circuits in one persistent
+launch captured in a CUDA graph. Each job must match the oracle (FP64
+1e-12) and the single-state path, alone and in the mix."""
+import numpy as np
+import pytest
+
+from oracle import dm_oracle as O
+from paper_2404_13184_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+def _jobs(count, n_lo, n_hi, seed, depth=(10, 40)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        d = int(rng.integers(*depth))
+        p = float(10 ** rng.uniform(-4, -2))
+        c = W.random_noisy_circuit(n, d, int(rng.integers(1 << 30)), gate_set=("h", "rz", "rx", "cx", "su2"),
+                                   p1=p, p2=p, gamma=1e-3)
+        masks = [1, (1 << n) - 1] + ([0b11] if n > 1 else [])
+        out.append((n, c.ops, masks))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_batch_matches_oracle_and_replays(tq, precision):
+    jobs = _jobs(24, 2, 8, 1)        # resident (n <= 6) and tiled (7, 8) jobs
+    b = tq.Batch(precision)
+    for n, ops, masks in jobs:
+        b.add(n, ops, width=-1, masks=masks)
+    tol = TOL64 if precision == "fp64" else 2e-6
+    for rep in range(2):                 # first run captures the graph, the second replays it
+        b.run()
+        b.wait()
+        info = b.info()
+        assert info["jobs"] == len(jobs) and info["items"] > 0
+        for j, (n, ops, masks) in enumerate(jobs):
+            want = O.run_circuit(n, ops)
+            got = b.rho(j)
+            assert np.max(np.abs(got - want)) < tol, (rep, j, n)
+            res = b.result(j)
+            assert abs(res[0] - O.trace(want).real) < (TOL64 if precision == "fp64" else 1e-5)
+            for i, m in enumerate(masks):
+                wz = O.expect_z(want, m) / (1.0 if precision == "fp64" else O.trace(want).real)
+                assert abs(res[2 + i] - wz) < (TOL64 if precision == "fp64" else 1e-5)
+    b.free()
+
+
+def test_batch_job_alone_equals_in_mix_and_single_state(tq):
+    jobs = _jobs(40, 4, 9, 2, depth=(20, 60))
+    mix = tq.Batch("fp64")
+    for n, ops, masks in jobs:
+        mix.add(n, ops, width=2, masks=masks)
+    mix.run()
+    mix.wait()
+    for j in (0, 7, 19, 33):
+        n, ops, masks = jobs[j]
+        alone = tq.Batch("fp64")
+        alone.add(n, ops, width=2, masks=masks)
+        alone.run()
+        alone.wait()
+        assert np.array_equal(alone.rho(0), mix.rho(j))          # bitwise: same kernels, same order
+        assert np.array_equal(alone.result(0), mix.result(j))
+        with tq.State(n, "fp64") as st:
+            st.run(ops, width=2)
+            assert np.array_equal(st.rho(), mix.rho(j))
+        alone.free()
+    mix.free()
+
+
+@pytest.mark.parametrize("tile_log2", [4, 8, 12, 18])
+def test_batch_tile_sizes_agree(tq, tile_log2):
+    jobs = _jobs(6, 7, 9, 3)
+    ref = tq.Batch("fp64")
+    tb = tq.Batch("fp64")
+    for n, ops, masks in jobs:
+        ref.add(n, ops, width=2, masks=masks)
+        tb.add(n, ops, width=2, masks=masks)
+    for n in (7, 8, 9):
+        tb.set_tile(n, tile_log2)
+    ref.run()
+    tb.run()
+    for j in range(len(jobs)):
+        assert np.array_equal(ref.rho(j), tb.rho(j))
+    ref.free()
+    tb.free()
+
+
+def test_batch_rejects_wide_blocks(tq):
+    b = tq.Batch("fp64")
+    ops = [("h", [0], ()), ("cx", [0, 1], ())]
+    with pytest.raises(tq.TqError) as e:
+        b.add(3, ops, width=3)
+    assert e.value.status == 7          # TQ_ERR_UNSUPPORTED
+    U = np.eye(8, dtype=complex)
+    with pytest.raises(tq.TqError) as e:
+        b.add(4, [("unitary", [0, 1, 2], [U])], width=2)
+    assert e.value.status == 7
+    b.free()
+
+
+def test_batch_wait_timeout_is_reported_and_recoverable(tq):
+    # a job whose device-side waits can never be satisfied: the bounded wait
+    # runs out, the kernel sets its error flag and returns normally
+    jobs = _jobs(4, 8, 8, 4)
+    b = tq.Batch("fp64")
+    for n, ops, masks in jobs:
+        b.add(n, ops, width=2, masks=masks)
+    b.test_wait_limit(20000, never_ready_job=1)
+    b.run()
+    with pytest.raises(tq.TqError) as e:
+        b.wait()
+    assert e.value.status == 5          # TQ_ERR_TIMEOUT
+    # the context is still usable: normal waits give correct results
+    b.test_wait_limit(20000000, never_ready_job=-1)
+    b.run()
+    b.wait()
+    for j, (n, ops, masks) in enumerate(jobs):
+        assert np.max(np.abs(b.rho(j) - O.run_circuit(n, ops))) < TOL64
+    b.free()
+    with tq.State(3, "fp64") as st:      # and other work still runs
+        st.run(W.ghz(3), width=2)
+        assert abs(st.trace() - 1) < TOL64

@@ -1,0 +1,116 @@
+"""Serving loop (tq_server): continuous batching of circuit requests. Each
+request's result must be the same alone and in the mix (FP64: bitwise; the
+arithmetic per group is identical), admission must respect the HBM budget,
+and results must match the oracle."""
+import numpy as np
+import pytest
+
+from oracle import dm_oracle as O
+from paper_2404_13184_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+def _requests(count, seed, n_lo=2, n_hi=9):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        c = W.served_request(rng, n_min=n_lo, n_max=n_hi, d_min=10, d_max=80)
+        out.append((c.n, c.ops, [1, (1 << c.n) - 1]))
+    return out
+
+
+def _single(tq, precision, n, ops, masks):
+    with tq.State(n, precision) as st:
+        st.run(ops, width=2)
+        tr = st.trace()
+        return np.concatenate([[tr.real, tr.imag], st.expect_z(masks)])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_served_results_same_alone_and_in_mix(tq, precision):
+    reqs = _requests(16, 5)
+    srv = tq.Server(precision, rho_budget=64 << 20, max_live=6)
+    ids = []
+    # arrivals spread over ticks: four requests join before every tick
+    pending = list(range(len(reqs)))
+    done = {}
+    ticks = 0
+    while (pending or len(done) < len(reqs)) and ticks < 10000:
+        for _ in range(4):
+            if pending:
+                k = pending.pop(0)
+                n, ops, masks = reqs[k]
+                ids.append((k, srv.submit(n, ops, width=2, masks=masks)))
+        live, queued, fin = srv.step()
+        assert live <= 6
+        ticks += 1
+        for k, rid in ids:
+            if k not in done:
+                st, res = srv.poll(rid)
+                if st == 2:
+                    done[k] = res
+    assert len(done) == len(reqs)
+    assert srv.info()["rho_live_bytes"] == 0
+    for k, (n, ops, masks) in enumerate(reqs):
+        alone = _single(tq, precision, n, ops, masks)
+        got = done[k].copy()
+        if precision == "split":
+            got[2:] = got[2:]                         # both already renormalised by the trace
+            assert np.max(np.abs(got - alone)) < 1e-6
+        else:
+            assert np.array_equal(got, alone), k
+            want = O.run_circuit(n, ops)
+            assert abs(got[0] - O.trace(want).real) < TOL64
+            for i, m in enumerate(masks):
+                assert abs(got[2 + i] - O.expect_z(want, m)) < TOL64
+    srv.free()
+
+
+def test_admission_respects_the_hbm_budget(tq):
+    # room for exactly two 8-qubit FP64 density matrices (1 MiB each): at most
+    # two requests can be admitted (and so finish) per tick
+    srv = tq.Server("fp64", rho_budget=2 << 20, max_live=8)
+    c = W.random_noisy_circuit(8, 30, 9)
+    ids = [srv.submit(8, c.ops, width=2, masks=[3]) for _ in range(5)]
+    finished_per_tick = []
+    guard = 0
+    while any(srv.poll(i)[0] != 2 for i in ids) and guard < 1000:
+        live, queued, fin = srv.step()
+        finished_per_tick.append(fin)
+        assert live + fin <= 2
+        assert srv.info()["rho_live_bytes"] <= 2 << 20
+        guard += 1
+    assert max(finished_per_tick) == 2 and len(finished_per_tick) == 3
+    want = O.run_circuit(8, c.ops)
+    for i in ids:
+        st, res = srv.poll(i)
+        assert st == 2 and abs(res[2] - O.expect_z(want, 3)) < TOL64
+    with pytest.raises(tq.TqError) as e:
+        srv.submit(10, c.ops, width=2)                 # 16 MiB can never fit a 2 MiB budget
+    assert e.value.status == 3                          # TQ_ERR_OOM
+    srv.free()
+
+
+def test_long_requests_stay_live_across_ticks(tq):
+    # 12-qubit requests advance 8 blocks per tick: they stay resident over
+    # several ticks while short ones arriving later finish first
+    srv = tq.Server("fp64", rho_budget=1 << 30, max_live=8)
+    long_c = W.random_noisy_circuit(12, 200, 21, gate_set=("h", "rz", "cx"))
+    short_c = W.random_noisy_circuit(5, 20, 22)
+    a = srv.submit(12, long_c.ops, width=2, masks=[1])
+    srv.step()
+    assert srv.poll(a)[0] == 1
+    b = srv.submit(5, short_c.ops, width=2, masks=[1])
+    srv.step()
+    assert srv.poll(b)[0] == 2 and srv.poll(a)[0] == 1
+    guard = 0
+    while srv.poll(a)[0] != 2 and guard < 1000:
+        srv.step()
+        guard += 1
+    res = srv.poll(a)[1]
+    with tq.State(12, "fp64") as st:
+        st.run(long_c.ops, width=2)
+        assert abs(res[2] - st.expect_z([1])[0]) < TOL64   # readouts reduce in a different order
+    srv.free()
