@@ -49,6 +49,7 @@ UNIT = "noisy gates/s"
 N_QUBITS = 15
 ZZ_MASK = 0b11
 SAMPLE_QUBITS = 12      # register size of the CPU-oracle sample
+SEED_SERVE = 2404_13184 + 5
 
 
 def peaks():
@@ -240,6 +241,126 @@ def cpu_sample_rate(pairs: int = 1):
     return raw * 4.0 ** (-(N_QUBITS - n)), raw, dt
 
 
+def autotune_cache():
+    return os.path.join(ROOT, "paper_2404_13184_gb300", "autotune_cache.txt")
+
+
+def run_sweep(tq, torch, precision, steps, warmup, count=1024, oracle_sample=12):
+    """Batched sweep: `count` independent noisy circuits (n ~ U{4..11}, depth
+    ~ U{50..500}, {H, RZ, RX, CX}, per-circuit depolarising p) in one
+    persistent launch per run (a CUDA graph replay), tile and fusion width per
+    qubit count from the autotuner. Returns throughput, per-circuit readouts
+    and the oracle error on a sample of the small circuits."""
+    from paper_2404_13184_gb300 import workloads
+    circuits = workloads.sweep(count)
+    t_tune = time.perf_counter()
+    tuned = {n: tq.autotune(precision, n, autotune_cache()) for n in sorted({c.n for c in circuits})}
+    t_tune = time.perf_counter() - t_tune
+    b = tq.Batch(precision)
+    for c in circuits:
+        b.add(c.n, c.ops, width=tuned[c.n][1], masks=[1, 3])
+    for n, (tile, _, _) in tuned.items():
+        b.set_tile(n, tile)
+    for _ in range(max(1, warmup)):
+        b.run()
+        b.wait()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        b.run()
+    e1.record(stream)
+    b.wait()
+    ms = e0.elapsed_time(e1) / steps
+    results = [b.result(j) for j in range(len(circuits))]
+    err = None
+    if oracle_sample:
+        from oracle import dm_oracle
+        small = [j for j, c in enumerate(circuits) if c.n <= 6][:oracle_sample]
+        e_tr, e_z = 0.0, 0.0
+        for j in small:
+            rho = dm_oracle.run_circuit(circuits[j].n, circuits[j].ops)
+            tr = dm_oracle.trace(rho).real
+            e_tr = max(e_tr, abs(results[j][0] - tr))
+            norm = 1.0 if precision == "fp64" else tr
+            e_z = max(e_z, abs(results[j][2] - dm_oracle.expect_z(rho, 1) / norm),
+                      abs(results[j][3] - dm_oracle.expect_z(rho, 3) / norm))
+        err = {"circuits_checked": len(small), "max_abs_trace_err": e_tr, "max_abs_z_err": e_z}
+    info = b.info()
+    b.free()
+    gates = sum(c.n_gates for c in circuits)
+    return {"ms_per_run": ms, "circuits_per_s": count / (ms / 1e3), "gates_per_s": gates / (ms / 1e3),
+            "circuits": count, "noisy_gates": gates, "items": info["items"], "rho_bytes": info["rho_bytes"],
+            "autotune": {str(n): {"tile_log2": t, "width": w, "ms": round(m, 3)} for n, (t, w, m) in tuned.items()},
+            "autotune_s": t_tune, "oracle_check": err, "results": results}
+
+
+def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=150 << 30, max_live=64):
+    """Poisson arrivals (`rate` per second for `duration` s) of random noisy
+    circuits (n ~ U{5..15}, depth ~ U{50..2000}, 30% CX, depolarising and
+    amplitude damping per request) served by the continuous-batching loop.
+    The FIFO queue is kept in arrival order; a request is materialised and
+    handed to the server when it reaches the head (a lookahead of 8), and its
+    latency is measured from its arrival time. Requests unfinished when the
+    drain window ends are censored."""
+    import numpy as np
+    from paper_2404_13184_gb300 import workloads
+    arrivals = workloads.poisson_arrivals(rate, duration, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    srv = tq.Server(precision, rho_budget=rho_budget, table_budget=8 << 30, max_live=max_live)
+    t0 = time.perf_counter()
+    nxt = 0
+    inflight = {}            # rid -> (arrival time, n, depth)
+    lat, done_n = [], []
+    queued_in_server = 0
+    busy = 0.0
+    while True:
+        now = time.perf_counter() - t0
+        if now > duration + drain:
+            break
+        while nxt < len(arrivals) and arrivals[nxt] <= now and queued_in_server < 8:
+            c = workloads.served_request(rng)
+            rid = srv.submit(c.n, c.ops, width=2, masks=[1])
+            inflight[rid] = (arrivals[nxt], c.n, c.n_gates)
+            nxt += 1
+            queued_in_server += 1
+        if not inflight:
+            if nxt >= len(arrivals):
+                break
+            time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+            continue
+        ts = time.perf_counter()
+        live, queued_in_server, fin = srv.step()
+        busy += time.perf_counter() - ts
+        if fin:
+            tdone = time.perf_counter() - t0
+            for rid in list(inflight):
+                st, _ = srv.poll(rid)
+                if st == 2:
+                    arr, n, d = inflight.pop(rid)
+                    lat.append(tdone - arr)
+                    done_n.append(n)
+    wall = time.perf_counter() - t0
+    end = wall
+    censored = [end - a for a, _, _ in inflight.values()] + [end - a for a in arrivals[nxt:] if a <= end]
+    info = srv.info()
+    srv.free()
+    lat_sorted = sorted(lat)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(q * len(v)))] if v else None
+    return {"precision": precision, "rate_per_s": rate, "arrival_window_s": duration, "drain_s": drain,
+            "arrived": sum(1 for a in arrivals if a <= end), "completed": len(lat),
+            "circuits_per_s": len(lat) / wall, "p50_latency_s": pct(lat_sorted, 0.5),
+            "p99_latency_s": pct(lat_sorted, 0.99), "censored": len(censored),
+            "censored_min_latency_s": min(censored) if censored else None,
+            "completed_qubit_counts": {str(k): done_n.count(k) for k in sorted(set(done_n))},
+            "gpu_busy_frac": busy / wall, "ticks": info["ticks"], "blocks_applied": info["blocks_applied"],
+            "sustainable_rate_per_s": len(lat) / max(busy, 1e-9)}
+
+
 def reference_arm(args, world, rank):
     if rank != 0:
         return 0
@@ -277,6 +398,14 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 leg (default --steps)")
     ap.add_argument("--n-qubits", type=int, default=15, help="register size (15 for the benchmark; smaller "
                     "registers for profiling captures)")
+    ap.add_argument("--workload", default="tfim15", choices=["tfim15", "sweep", "serve"],
+                    help="tfim15: the benchmark line; sweep / serve: the batched-sweep and served-stream workloads")
+    ap.add_argument("--precision", default="both", choices=["fp64", "split", "both"], help="sweep / serve modes")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-duration", type=float, default=60.0)
+    ap.add_argument("--serve-drain", type=float, default=60.0)
+    ap.add_argument("--serve-in-line", type=float, default=15.0,
+                    help="seconds of split-precision served stream added to the tfim15 line (0: none)")
     args = ap.parse_args()
     global N_QUBITS
     N_QUBITS = args.n_qubits
@@ -298,6 +427,22 @@ def main():
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis and vis.split(",")[0].strip().isdigit():
         gpu_index = int(vis.split(",")[local].strip())
+
+    if args.workload in ("sweep", "serve"):
+        precs = ["fp64", "split"] if args.precision == "both" else [args.precision]
+        for prec in precs:
+            if args.workload == "sweep":
+                r = run_sweep(tq, torch, prec, args.steps, args.warmup)
+                r.pop("results")
+                line = {"metric": "batched sweep circuits/s", "workload": "sweep-1024 (n 4-11, depth 50-500)",
+                        "dtype": "f64" if prec == "fp64" else "f32", **r}
+            else:
+                r = run_serve(tq, prec, args.serve_rate, args.serve_duration, args.serve_drain)
+                line = {"metric": "served circuits/s + p99 latency", "workload": "poisson-served (n 5-15, depth "
+                        "50-2000)", "dtype": "f64" if prec == "fp64" else "f32", **r}
+            if rank == 0:
+                print(json.dumps(line), flush=True)
+        return 0
 
     K, W = args.steps, args.warmup
     K64 = args.fp64_steps or K
@@ -364,6 +509,8 @@ def main():
                                       "avg_launch_ms": ss["total_ms"] / ss["launches"],
                                       "peak_source": f"{peak_src} HBM copy bandwidth"},
                          "gpu_launches": split["launches"]}
+    if args.serve_in_line > 0 and not args.no_split:
+        line["serve"] = run_serve(tq, "split", args.serve_rate, args.serve_in_line, args.serve_in_line)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         scaled, raw, dt = cpu_sample_rate(2)
         line["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",

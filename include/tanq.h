@@ -276,6 +276,17 @@ tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size
 
 void tq_batch_free(tq_batch* b);
 
+/* Autotuner of the batch engine: times every (fusion width in {1, 2},
+ * entries per tile) candidate for n_qubits (2..14) at this precision on a
+ * synthetic batch of random depolarised {H, RZ, RX, CX} circuits (about
+ * 2^24 density-matrix entries in total, depth 64) and returns the fastest
+ * (*ms_out: its time per run). With cache_path not NULL, a cached result for
+ * this GPU name, precision and n is returned without timing, and a new
+ * result is appended to the file ("<gpu> <precision> <n> <tile_log2>
+ * <width> <ms>" per line). */
+tq_status tq_autotune(int precision, int n_qubits, const char* cache_path, int* tile_log2_out,
+                      int* width_out, double* ms_out);
+
 /* ---- serving loop (continuous batching of circuit requests) --------------
  * Requests (independent circuits, each on its own |0..0><0..0|) wait in a
  * FIFO queue. A request is admitted, in order, when its density matrix fits

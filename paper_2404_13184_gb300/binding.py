@@ -80,6 +80,7 @@ _SIGNATURES = [
     ("tq_batch_get_rho", c_int, [c_void_p, c_int, POINTER(c_double)]),
     ("tq_batch_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_size_t)]),
     ("tq_batch_free", None, [c_void_p]),
+    ("tq_autotune", c_int, [c_int, c_int, ctypes.c_char_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     ("tq_server_create", c_int, [c_int, c_void_p, c_size_t, c_size_t, c_int, POINTER(c_void_p)]),
     ("tq_server_submit", c_int, [c_void_p, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_uint64), c_int,
                                  POINTER(c_int)]),
@@ -253,6 +254,15 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+def autotune(precision: str, n: int, cache_path: str | None = None):
+    """(tile_log2, fusion width, ms per run) for the batch engine at n qubits."""
+    lib = load()
+    t, w, ms = c_int(0), c_int(0), c_double(0)
+    _check(lib.tq_autotune(PRECISION[precision], n, cache_path.encode() if cache_path else None, ctypes.byref(t),
+                           ctypes.byref(w), ctypes.byref(ms)), "tq_autotune")
+    return t.value, w.value, ms.value
 
 
 class Server:

@@ -124,3 +124,24 @@ def test_batch_wait_timeout_is_reported_and_recoverable(tq):
     with tq.State(3, "fp64") as st:      # and other work still runs
         st.run(W.ghz(3), width=2)
         assert abs(st.trace() - 1) < TOL64
+
+
+def test_autotune_picks_a_valid_candidate_and_caches(tq, tmp_path):
+    cache = str(tmp_path / "tune.txt")
+    t, w, ms = tq.autotune("fp64", 8, cache)
+    assert w in (1, 2) and 4 <= t <= 16 and ms > 0
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].split()[1:3] == ["fp64", "8"]
+    assert tq.autotune("fp64", 8, cache) == (t, w, ms)          # answered from the cache
+    assert len(open(cache).read().splitlines()) == 1
+    # the tuned settings give the same results as the defaults
+    jobs = _jobs(5, 8, 8, 11)
+    a, b = tq.Batch("fp64"), tq.Batch("fp64")
+    for n, ops, masks in jobs:
+        a.add(n, ops, width=w, masks=masks)
+        b.add(n, ops, width=w, masks=masks)
+    b.set_tile(8, t)
+    a.run()
+    b.run()
+    for j in range(len(jobs)):
+        assert np.array_equal(a.rho(j), b.rho(j))
