@@ -143,6 +143,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(v, world, device="cuda"):
+    """Max of a per-rank time over all ranks (the job takes as long as its
+    slowest replica); identity on one rank."""
+    if world == 1 or v is None:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, max_ms, world):
+    """Whole-job rate: units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def step_ops():
     from paper_2404_13184_gb300 import workloads
     return workloads.tfim_ring(N_QUBITS, steps=1).ops
@@ -361,6 +378,41 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
             "sustainable_rate_per_s": len(lat) / max(busy, 1e-9)}
 
 
+def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12):
+    """Layered thermal-relaxation workload (n = 12: 2^24 entries, 2000 gates):
+    time of the whole circuit per fusion width (0 = unfused plain path) and
+    the max-abs difference of <Z_i> and sampled vec(rho) entries to the
+    unfused FP64 result."""
+    import numpy as np
+    from paper_2404_13184_gb300 import workloads
+    c = workloads.layered_thermal(n=n)
+    masks = [1 << q for q in range(n)]
+    ref_z, ref_v, out = None, None, {}
+    idx = np.random.default_rng(0).integers(0, 1 << (2 * n), 4096)
+    for w in widths:
+        prog = tq.DeviceProgram(n, c.ops, width=w, precision=precision)
+        st = tq.State(n, precision)
+        st.run_program(prog)                      # warm-up
+        st.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.run_program(prog)
+        z = st.expect_z(masks)
+        dt = time.perf_counter() - t0
+        v = st.vec()[idx]
+        if ref_z is None:
+            ref_z, ref_v = z, v
+        out[str(w)] = {"blocks": prog.n_blocks, "ms": dt * 1e3, "gates_per_s": c.n_gates / dt,
+                       "max_abs_z_diff_vs_unfused": float(np.max(np.abs(z - ref_z))),
+                       "max_abs_rho_diff_vs_unfused": float(np.max(np.abs(v - ref_v)))}
+        st.free()
+        prog.free()
+    base = out[str(widths[0])]["ms"]
+    for w in out:
+        out[w]["speedup_vs_unfused"] = base / out[w]["ms"]
+    return {"n_qubits": n, "noisy_gates": c.n_gates, "widths": out}
+
+
 def reference_arm(args, world, rank):
     if rank != 0:
         return 0
@@ -398,7 +450,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 leg (default --steps)")
     ap.add_argument("--n-qubits", type=int, default=15, help="register size (15 for the benchmark; smaller "
                     "registers for profiling captures)")
-    ap.add_argument("--workload", default="tfim15", choices=["tfim15", "sweep", "serve"],
+    ap.add_argument("--workload", default="tfim15", choices=["tfim15", "sweep", "serve", "layered12"],
                     help="tfim15: the benchmark line; sweep / serve: the batched-sweep and served-stream workloads")
     ap.add_argument("--precision", default="both", choices=["fp64", "split", "both"], help="sweep / serve modes")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -428,6 +480,15 @@ def main():
     if vis and vis.split(",")[0].strip().isdigit():
         gpu_index = int(vis.split(",")[local].strip())
 
+    if args.workload == "layered12":
+        precs = ["fp64", "split"] if args.precision == "both" else [args.precision]
+        for prec in precs:
+            r = run_layered(tq, torch, prec)
+            if rank == 0:
+                print(json.dumps({"metric": "layered thermal circuit: time per fusion width", "workload":
+                                  "layered-thermal-12q-2000g", "dtype": "f64" if prec == "fp64" else "f32", **r}),
+                      flush=True)
+        return 0
     if args.workload in ("sweep", "serve"):
         precs = ["fp64", "split"] if args.precision == "both" else [args.precision]
         for prec in precs:
@@ -451,15 +512,8 @@ def main():
     split = None if args.no_split else run_device_leg(tq, torch, "split", K, W, world)
     e2e_ms = None if args.no_e2e else run_e2e_leg(tq, torch, "fp64", K64, W, world)
 
-    def max_over_ranks(v):
-        if world == 1 or v is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms64 = max_over_ranks(fp64["ms"])
-    value = world * K64 * gates_per_step / (ms64 / 1e3)
+    ms64 = max_over_ranks(fp64["ms"], world)
+    value = job_throughput(K64 * gates_per_step, ms64, world)
     clk = fp64["clocks"] or {}
     sm_mhz = clk.get("sm_mhz") or sm_max_cfg
     name64, st64 = dominant(fp64["stats"])
@@ -489,13 +543,13 @@ def main():
             "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)}
                         for k, v in fp64["stats"].items()}}
     if e2e_ms is not None:
-        e2e_ms = max_over_ranks(e2e_ms)
-        line["e2e"] = {"value": world * K64 * gates_per_step / (e2e_ms / 1e3), "unit": UNIT,
+        e2e_ms = max_over_ranks(e2e_ms, world)
+        line["e2e"] = {"value": job_throughput(K64 * gates_per_step, e2e_ms, world), "unit": UNIT,
                        "h2d_bytes_per_step": fp64["table_bytes"] + 8, "d2h_bytes_per_step": 3 * 8,
                        "ms_per_step": e2e_ms / K64}
     if split is not None:
-        mss = max_over_ranks(split["ms"])
-        vs = world * K * gates_per_step / (mss / 1e3)
+        mss = max_over_ranks(split["ms"], world)
+        vs = job_throughput(K * gates_per_step, mss, world)
         ns, ss = dominant(split["stats"])
         ach = ss["bytes"] * ss["launches"] / (ss["total_ms"] / 1e3) / 1e9
         n_cmp = min(len(split["zz"]), len(fp64["zz"]))

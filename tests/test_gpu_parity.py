@@ -306,3 +306,26 @@ def test_profile_counts_launches(tq):
     assert stats["apply_f64_w2"]["flops"] == 8.0 * 4 ** n * 16
     assert stats["apply_f64_w2"]["bytes"] == 2 * 16 * 4 ** n
     assert all(v["total_ms"] > 0 for v in stats.values())
+
+
+def test_layered_thermal_12q_fusion_widths_agree(tq):
+    # the 12-qubit layered thermal workload at full register size (first 400
+    # gates): every fusion width gives the unfused result within 1e-12
+    import torch
+    c = W.layered_thermal(n=12, n_gates=400)
+    masks = [1 << q for q in range(12)] + [0b11, (1 << 12) - 1]
+    idx = torch.as_tensor(np.random.default_rng(1).integers(0, 1 << 24, 8192), device="cuda")
+    ref = None
+    for width in (0, 1, 2, 3, 4):
+        with tq.State(12, "fp64") as st:
+            nb = st.run(c.ops, width=width)
+            z = st.expect_z(masks)
+            tr = st.trace()
+            v = st._buf.view(torch.complex128)[idx].cpu().numpy()
+        assert abs(tr - 1) < 1e-11
+        if ref is None:
+            ref = (z, v, nb)
+            continue
+        assert nb < ref[2]
+        assert maxabs(z, ref[0]) < TOL64, width
+        assert maxabs(v, ref[1]) < TOL64, width
