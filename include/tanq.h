@@ -147,8 +147,25 @@ tq_status tq_info(const tq_state* s, int* n_qubits, int* precision);
 tq_status tq_reset(tq_state* s);
 
 /* Device address of vec(rho) (complex128 or complex64, interleaved), for
- * zero-copy interop on the state's stream. */
+ * zero-copy interop on the state's stream. All 4^n entries are current once
+ * work enqueued before this call completes (in Hermitian mode the lower
+ * triangle is filled first, asynchronously on the stream). */
 tq_status tq_rho_device_ptr(tq_state* s, void** out);
+
+/* Hermitian mode (FP64 states; on by default). Every op is a Kraus map,
+ * which keeps rho = rho^dagger, so the group with row-rest bits a and
+ * column-rest bits b is the conjugate transpose of group (b, a): only the
+ * groups with a <= b are computed and only entries with row <= column are
+ * kept current, halving the work of every apply pass. The diagonal, hence
+ * every readout, is always current; tq_get_rho and tq_rho_device_ptr fill
+ * the lower triangle first. The mode is active only while rho is known to
+ * be Hermitian: from tq_create/tq_reset on, and after tq_set_rho only if
+ * max |rho - rho^dagger| <= 4 eps max |rho| (checked on the GPU). on = 0
+ * turns it off (full updates). */
+tq_status tq_set_hermitian(tq_state* s, int on);
+
+/* *active = 1 if apply passes currently use Hermitian mode. */
+tq_status tq_is_hermitian_mode(const tq_state* s, int* active);
 
 /* Copy vec(rho) out to / in from host memory: 2 * 4^n doubles, interleaved
  * (re, im) in vec order (index r + c 2^n). Split states convert from/to

@@ -56,6 +56,8 @@ _SIGNATURES = [
     ("tq_info", c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     ("tq_reset", c_int, [c_void_p]),
     ("tq_rho_device_ptr", c_int, [c_void_p, POINTER(c_void_p)]),
+    ("tq_set_hermitian", c_int, [c_void_p, c_int]),
+    ("tq_is_hermitian_mode", c_int, [c_void_p, POINTER(c_int)]),
     ("tq_get_rho", c_int, [c_void_p, POINTER(c_double)]),
     ("tq_set_rho", c_int, [c_void_p, POINTER(c_double)]),
     ("tq_apply_gate", c_int, [c_void_p, POINTER(c_int), c_int, POINTER(c_double)]),
@@ -381,7 +383,8 @@ def _torch_plumbing():
 class State:
     """A density matrix on the GPU (tq_state)."""
 
-    def __init__(self, n: int, precision: str = "fp64", stream=None, torch_memory: bool = True):
+    def __init__(self, n: int, precision: str = "fp64", stream=None, torch_memory: bool = True,
+                 hermitian: bool = True):
         lib = load()
         self.n = n
         self.precision = precision
@@ -399,6 +402,16 @@ class State:
                                     ctypes.byref(self._h)), "tq_create_on")
         else:
             _check(lib.tq_create(n, prec, c_void_p(stream), ctypes.byref(self._h)), "tq_create")
+        if not hermitian:
+            _check(lib.tq_set_hermitian(self._h, 0), "tq_set_hermitian")
+
+    def set_hermitian(self, on: bool):
+        _check(_lib.tq_set_hermitian(self._h, 1 if on else 0), "tq_set_hermitian")
+
+    def hermitian_mode(self) -> bool:
+        v = c_int(0)
+        _check(_lib.tq_is_hermitian_mode(self._h, ctypes.byref(v)), "tq_is_hermitian_mode")
+        return bool(v.value)
 
     # -- lifetime
     def free(self):

@@ -1,6 +1,15 @@
 // Apply kernels: one pass of a fused width-K superoperator over vec(rho)
 // (TANQ-Sim Sec. 3.1, the C1/C2 update generalised to K <= 4).
 //
+// Hermitian mode (FP64 states): every op is a Kraus map, which keeps
+// rho = rho^dagger. Writing a group's rest bits as (a, b) = (row rest,
+// column rest), group (b, a) holds the conjugate transposes of group (a, b),
+// so only the canonical groups a <= b are computed and only entries with
+// row <= column are kept current: an input below the diagonal is read as
+// the conjugate of its transpose, an output below the diagonal is written,
+// conjugated, to its transpose. The diagonal (all readouts) is always
+// current; tq_get_rho fills the lower triangle before copying out.
+//
 // vec(rho) has 4^n entries; a width-K block on qubits q_0..q_{K-1} splits the
 // 2n index bits into 2K target bits (q_j and q_j + n) and 2n - 2K group bits.
 // Group g's base index is g with zeros inserted at the target bits; its 4^K
@@ -65,34 +74,74 @@ struct CplxOps<float2> {
 // Grid-stride over groups; consecutive threads take consecutive groups, so a
 // warp's loads of one local index are contiguous whenever the low index bits
 // are group bits.
-template <typename T2, int K>
-__global__ void __launch_bounds__(256) k_apply_direct(T2* rho, const T2* __restrict__ S,
-                                                      const __grid_constant__ ApplyParams p) {
+template <typename T2, int K, bool HERM>
+__device__ __forceinline__ void apply_direct_body(T2* rho, const T2* __restrict__ S, const ApplyParams& p) {
   constexpr int D = 1 << (2 * K);
   __shared__ T2 sS[D * D];
   for (int i = threadIdx.x; i < D * D; i += blockDim.x) sS[i] = S[i];
   __syncthreads();
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < p.n_groups;
-       g += stride) {
-    unsigned long long base = g;
+  const unsigned long long total = HERM ? p.n_canon : p.n_groups;
+  const unsigned long long rmask = (1ull << p.n) - 1ull;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total; t += stride) {
+    bool self = false;
+    unsigned long long base = HERM ? canonical_group(t, p.n - K, &self) : t;
 #pragma unroll
     for (int i = 0; i < 2 * K; ++i) {
       const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
       base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
     }
     T2 x[D];
+    if (!HERM) {
 #pragma unroll
-    for (int l = 0; l < D; ++l) x[l] = rho[base + p.off[l]];
+      for (int l = 0; l < D; ++l) x[l] = rho[base + p.off[l]];
+    } else {
+      // entries below the diagonal are read as the conjugate of their transpose
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const unsigned long long e = base + p.off[l], r = e & rmask, c = e >> p.n;
+        const bool up = r <= c;
+        T2 v = rho[up ? e : (c | (r << p.n))];
+        if (!up) v.y = -v.y;
+        x[l] = v;
+      }
+    }
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       T2 acc = CplxOps<T2>::zero();
 #pragma unroll
       for (int j = 0; j < D; ++j)
         CplxOps<T2>::fma(acc, K == 1 ? sS[i * D + j] : CplxOps<T2>::lds(&sS[i * D + j]), x[j]);
-      rho[base + p.off[i]] = acc;
+      if (!HERM) {
+        rho[base + p.off[i]] = acc;
+      } else {
+        // outputs below the diagonal go, conjugated, to their transpose (which
+        // lies in the skipped partner group; in a self-conjugate group the
+        // transpose is written directly by its own row)
+        const unsigned long long e = base + p.off[i], r = e & rmask, c = e >> p.n;
+        if (r <= c) {
+          rho[e] = acc;
+        } else if (!self) {
+          acc.y = -acc.y;
+          rho[c | (r << p.n)] = acc;
+        }
+      }
     }
   }
+}
+
+template <typename T2, int K>
+__global__ void __launch_bounds__(256) k_apply_direct(T2* rho, const T2* __restrict__ S,
+                                                      const __grid_constant__ ApplyParams p) {
+  apply_direct_body<T2, K, false>(rho, S, p);
+}
+
+// Hermitian variant (FP64): the DFMA pipe needs few warps, so the extra
+// address registers of this path (one CTA per SM at width 2) cost nothing.
+template <typename T2, int K>
+__global__ void __launch_bounds__(256) k_apply_direct_herm(T2* rho, const T2* __restrict__ S,
+                                                              const __grid_constant__ ApplyParams p) {
+  apply_direct_body<T2, K, true>(rho, S, p);
 }
 
 // Widths 3 and 4: a CTA stages the entries of G consecutive groups (4^K x G)
@@ -100,7 +149,7 @@ __global__ void __launch_bounds__(256) k_apply_direct(T2* rho, const T2* __restr
 // (256/G) r of group gi and writes them straight back to global memory (the
 // tile's entries were all read before the first write). S sits in shared
 // memory when it fits (K = 3) and is read through L1/L2 otherwise (K = 4).
-template <typename T2, int K, int G, bool S_SMEM>
+template <typename T2, int K, int G, bool S_SMEM, bool HERM>
 __global__ void __launch_bounds__(256) k_apply_tiled(T2* rho, const T2* __restrict__ S,
                                                      const __grid_constant__ ApplyParams p) {
   constexpr int D = 1 << (2 * K);
@@ -124,17 +173,33 @@ __global__ void __launch_bounds__(256) k_apply_tiled(T2* rho, const T2* __restri
   __syncthreads();
   const int gi = threadIdx.x % G;
   const int rowset = threadIdx.x / G;
-  const unsigned long long n_tiles = (p.n_groups + G - 1) / G;
+  const unsigned long long total = HERM ? p.n_canon : p.n_groups;
+  const unsigned long long rmask = (1ull << p.n) - 1ull;
+  const unsigned long long n_tiles = (total + G - 1) / G;
   for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const unsigned long long g0 = tile * G;
     for (int e = threadIdx.x; e < D * G; e += blockDim.x) {
       const int l = e / G, gg = e % G;
-      const unsigned long long g = g0 + gg;
-      if (g < p.n_groups) sX[e] = rho[deposit_zeros(g, p.pos, 2 * K) + sOff[l]];
+      const unsigned long long t = g0 + gg;
+      if (t < total) {
+        bool self = false;
+        const unsigned long long g = HERM ? canonical_group(t, p.n - K, &self) : t;
+        const unsigned long long idx = deposit_zeros(g, p.pos, 2 * K) + sOff[l];
+        if (!HERM) {
+          sX[e] = rho[idx];
+        } else {
+          const unsigned long long r = idx & rmask, c = idx >> p.n;
+          T2 v = rho[r <= c ? idx : (c | (r << p.n))];
+          if (r > c) v.y = -v.y;
+          sX[e] = v;
+        }
+      }
     }
     __syncthreads();
-    const unsigned long long g = g0 + gi;
-    if (g < p.n_groups) {
+    const unsigned long long t = g0 + gi;
+    if (t < total) {
+      bool self = false;
+      const unsigned long long g = HERM ? canonical_group(t, p.n - K, &self) : t;
       const unsigned long long base = deposit_zeros(g, p.pos, 2 * K);
 #pragma unroll 1
       for (int r0 = 0; r0 < ROWS; r0 += CH) {
@@ -154,7 +219,19 @@ __global__ void __launch_bounds__(256) k_apply_tiled(T2* rho, const T2* __restri
 #pragma unroll
         for (int r = 0; r < CH; ++r) {
           const int i = rowset + ROWSETS * (r0 + r);
-          rho[base + sOff[i]] = acc[r];
+          const unsigned long long idx = base + sOff[i];
+          if (!HERM) {
+            rho[idx] = acc[r];
+          } else {
+            const unsigned long long rr = idx & rmask, cc = idx >> p.n;
+            if (rr <= cc) {
+              rho[idx] = acc[r];
+            } else if (!self) {
+              T2 v = acc[r];
+              v.y = -v.y;
+              rho[cc | (rr << p.n)] = v;
+            }
+          }
         }
       }
     }
@@ -168,28 +245,31 @@ size_t tiled_smem_bytes() {
   return D * sizeof(unsigned long long) + (size_t)D * G * sizeof(T2) + (S_SMEM ? (size_t)D * D * sizeof(T2) : 0);
 }
 
-template <typename T2, int K, int G, bool S_SMEM>
+template <typename T2, int K, int G, bool S_SMEM, bool HERM>
 cudaError_t run_tiled(T2* rho, const T2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
   static std::once_flag once;
   static int per_sm = 1;
   const size_t smem = tiled_smem_bytes<T2, K, G, S_SMEM>();
   std::call_once(once, [&] {
-    cudaFuncSetAttribute(k_apply_tiled<T2, K, G, S_SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_apply_tiled<T2, K, G, S_SMEM, HERM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apply_tiled<T2, K, G, S_SMEM>, 256, smem) == cudaSuccess && b > 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apply_tiled<T2, K, G, S_SMEM, HERM>, 256, smem) == cudaSuccess && b > 0)
       per_sm = b;
   });
-  const unsigned long long n_tiles = (p.n_groups + G - 1) / G;
+  const unsigned long long n_tiles = ((p.herm ? p.n_canon : p.n_groups) + G - 1) / G;
   const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_tiles, (unsigned long long)num_sms * per_sm));
-  k_apply_tiled<T2, K, G, S_SMEM><<<grid, 256, smem, st>>>(rho, S, p);
+  k_apply_tiled<T2, K, G, S_SMEM, HERM><<<grid, 256, smem, st>>>(rho, S, p);
   return cudaGetLastError();
 }
 
-template <typename T2, int K>
+template <typename T2, int K, bool HERM>
 cudaError_t run_direct(T2* rho, const T2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
-  const unsigned long long blocks = (p.n_groups + 255) / 256;
+  const unsigned long long blocks = ((p.herm ? p.n_canon : p.n_groups) + 255) / 256;
   const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(blocks, (unsigned long long)num_sms * 8));
-  k_apply_direct<T2, K><<<grid, 256, 0, st>>>(rho, S, p);
+  if (HERM)
+    k_apply_direct_herm<T2, K><<<grid, 256, 0, st>>>(rho, S, p);
+  else
+    k_apply_direct<T2, K><<<grid, 256, 0, st>>>(rho, S, p);
   return cudaGetLastError();
 }
 
@@ -200,20 +280,30 @@ cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyPar
   if (precision == 0) {
     double2* r = static_cast<double2*>(rho);
     const double2* s = static_cast<const double2*>(S);
-    switch (p.width) {
-      case 1: return run_direct<double2, 1>(r, s, p, num_sms, st);
-      case 2: return run_direct<double2, 2>(r, s, p, num_sms, st);
-      case 3: return run_tiled<double2, 3, 32, true>(r, s, p, num_sms, st);
-      case 4: return run_tiled<double2, 4, 16, false>(r, s, p, num_sms, st);
+    if (p.herm) {
+      switch (p.width) {
+        case 1: return run_direct<double2, 1, true>(r, s, p, num_sms, st);
+        case 2: return run_direct<double2, 2, true>(r, s, p, num_sms, st);
+        case 3: return run_tiled<double2, 3, 32, true, true>(r, s, p, num_sms, st);
+        case 4: return run_tiled<double2, 4, 16, false, true>(r, s, p, num_sms, st);
+      }
+    } else {
+      switch (p.width) {
+        case 1: return run_direct<double2, 1, false>(r, s, p, num_sms, st);
+        case 2: return run_direct<double2, 2, false>(r, s, p, num_sms, st);
+        case 3: return run_tiled<double2, 3, 32, true, false>(r, s, p, num_sms, st);
+        case 4: return run_tiled<double2, 4, 16, false, false>(r, s, p, num_sms, st);
+      }
     }
   } else {
     float2* r = static_cast<float2*>(rho);
     const float2* s = static_cast<const float2*>(S);
+    if (p.herm) return cudaErrorInvalidValue;  // split states always update every group
     switch (p.width) {
-      case 1: return run_direct<float2, 1>(r, s, p, num_sms, st);
-      case 2: return run_direct<float2, 2>(r, s, p, num_sms, st);
-      case 3: return run_tiled<float2, 3, 32, true>(r, s, p, num_sms, st);
-      case 4: return run_tiled<float2, 4, 32, false>(r, s, p, num_sms, st);
+      case 1: return run_direct<float2, 1, false>(r, s, p, num_sms, st);
+      case 2: return run_direct<float2, 2, false>(r, s, p, num_sms, st);
+      case 3: return run_tiled<float2, 3, 32, true, false>(r, s, p, num_sms, st);
+      case 4: return run_tiled<float2, 4, 32, false, false>(r, s, p, num_sms, st);
     }
   }
   return cudaErrorInvalidValue;

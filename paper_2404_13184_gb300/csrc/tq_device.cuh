@@ -53,7 +53,25 @@ struct ApplyParams {
   int pos[8];
   int q[4];
   unsigned long long off[16];
+  // Hermitian mode: rho = rho^dagger is kept exactly by computing only the
+  // canonical groups (row rest a <= column rest b, n_canon of them) and
+  // storing only entries with row <= column (see tq_apply.cu).
+  int herm;
+  int pad;
+  unsigned long long n_canon;
 };
+
+// Group index of the t-th canonical group (a <= b, enumerated column by
+// column: t = b (b + 1) / 2 + a); rest_bits = n - width.
+__host__ __device__ __forceinline__ unsigned long long canonical_group(unsigned long long t, int rest_bits,
+                                                                       bool* self) {
+  unsigned long long b = (unsigned long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while (b * (b + 1) / 2 > t) --b;
+  while ((b + 1) * (b + 2) / 2 <= t) ++b;
+  const unsigned long long a = t - b * (b + 1) / 2;
+  *self = a == b;
+  return a | (b << rest_bits);
+}
 
 // Insert a zero bit at each of the first `npos` positions of `pos`
 // (ascending): the base index of group g (Sec. 3.1, index s_i, generalised).
@@ -84,6 +102,11 @@ cudaError_t launch_diag_probs(const void* rho, int n, int precision, const doubl
                               double* out, cudaStream_t st);
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t count, cudaStream_t st);
 cudaError_t launch_convert_f32_to_f64(const float* in, double* out, size_t count, cudaStream_t st);
+// Hermitian mode helpers (FP64 states): fill every entry with row > column
+// from the conjugate of its transpose; and measure max |rho - rho^dagger| and
+// max |rho| (two doubles at out, as non-negative bit patterns via atomicMax).
+cudaError_t launch_mirror_lower(double2* rho, int n, cudaStream_t st);
+cudaError_t launch_hermiticity(const double2* rho, int n, double* out, cudaStream_t st);
 
 // --- apply kernels (tq_apply.cu) ------------------------------------------
 // One pass of a fused block over vec(rho). S: 4^K x 4^K superoperator,

@@ -194,6 +194,50 @@ __global__ void k_diag_probs(const T2* __restrict__ rho, int n, const double* __
     out[x] = (double)rho[x * (N + 1)].x * scale;
 }
 
+__global__ void k_mirror_lower(double2* rho, int n) {
+  const unsigned long long N = 1ull << n, total = N * N;
+  for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < total;
+       e += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = e & (N - 1), c = e >> n;
+    if (r > c) {
+      const double2 v = rho[c | (r << n)];
+      rho[e] = make_double2(v.x, -v.y);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_hermiticity(const double2* __restrict__ rho, int n, double* out) {
+  __shared__ double s_d[256], s_m[256];
+  const unsigned long long N = 1ull << n, total = N * N;
+  double d = 0.0, m = 0.0;
+  for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < total;
+       e += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = e & (N - 1), c = e >> n;
+    const double2 v = rho[e];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    if (r < c) {
+      const double2 w = rho[c | (r << n)];
+      d = fmax(d, fmax(fabs(v.x - w.x), fabs(v.y + w.y)));
+    } else if (r == c) {
+      d = fmax(d, fabs(v.y));
+    }
+  }
+  s_d[threadIdx.x] = d;
+  s_m[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      s_d[threadIdx.x] = fmax(s_d[threadIdx.x], s_d[threadIdx.x + s]);
+      s_m[threadIdx.x] = fmax(s_m[threadIdx.x], s_m[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(s_d[0]));
+    atomicMax(reinterpret_cast<unsigned long long*>(out + 1), (unsigned long long)__double_as_longlong(s_m[0]));
+  }
+}
+
 __global__ void k_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -259,6 +303,22 @@ cudaError_t launch_diag_probs(const void* rho, int n, int precision, const doubl
     k_diag_probs<double2><<<grid, 256, 0, st>>>((const double2*)rho, n, trace_or_null, out);
   else
     k_diag_probs<float2><<<grid, 256, 0, st>>>((const float2*)rho, n, trace_or_null, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_lower(double2* rho, int n, cudaStream_t st) {
+  const unsigned long long total = 1ull << (2 * n);
+  const int grid = (int)std::min<unsigned long long>(152 * 16, (total + 255) / 256);
+  k_mirror_lower<<<grid, 256, 0, st>>>(rho, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hermiticity(const double2* rho, int n, double* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const unsigned long long total = 1ull << (2 * n);
+  const int grid = (int)std::min<unsigned long long>(152 * 8, (total + 255) / 256);
+  k_hermiticity<<<grid, 256, 0, st>>>(rho, n, out);
   return cudaGetLastError();
 }
 

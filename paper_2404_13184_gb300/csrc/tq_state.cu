@@ -42,6 +42,10 @@ struct tq_state {
   PinBuf pin, pin_small;
   cudaEvent_t pin_free = nullptr;  // recorded after the last upload from `pin`
   tq_program scratch;              // plan of the last tq_run_circuit call
+  // Hermitian mode (FP64): half of the groups, entries with row <= column kept
+  bool herm_mode = true;     // allowed by the caller
+  bool herm_ok = true;       // rho is known to be Hermitian
+  bool lower_stale = false;  // entries with row > column are out of date
   uint64_t launches = 0;
   bool prof_on = false;
   std::vector<Pending> pending;
@@ -286,15 +290,26 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
   if (e == cudaSuccess)
     e = timed(s, K_FUSE, 1, [&] { return launch_fuse(sops, d_ops, d_blk, d_mem, d_work, P.n_work, sb64, sb32, s->stream); });
   const double entries = (double)(1ull << (2 * s->n));
+  const bool herm = s->prec == TQ_FP64 && s->herm_mode && s->herm_ok;
   for (size_t b = 0; b < P.params.size() && e == cudaSuccess; ++b) {
-    const ApplyParams& p = P.params[b];
+    ApplyParams p = P.params[b];
+    double groups = (double)p.n_groups;
+    if (herm) {
+      const unsigned long long M = 1ull << (s->n - p.width);
+      p.herm = 1;
+      p.n_canon = M * (M + 1) / 2;
+      groups = (double)p.n_canon;
+      s->lower_stale = true;
+    }
     const void* S = s->prec == TQ_FP64 ? (const void*)(sb64 + P.sb_off[b]) : (const void*)(sb32 + P.sb_off[b]);
     const int kind = (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
     e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream); });
-    if (s->prof_on) {
-      s->prof_flops[kind] = 8.0 * entries * (double)(1 << (2 * p.width));
-      s->prof_bytes[kind] = 2.0 * entries * (double)entry_bytes(s->prec);
+    if (s->prof_on) {  // per launch: the groups computed x (8 * 16^w flops, 2 * B * 4^w bytes) each
+      const double per = (double)(1 << (2 * p.width));
+      s->prof_flops[kind] = 8.0 * groups * per * per;
+      s->prof_bytes[kind] = 2.0 * groups * per * (double)entry_bytes(s->prec);
     }
+    (void)entries;
   }
   return cuda_fail(s, e);
 }
@@ -465,12 +480,39 @@ tq_status tq_reset(tq_state* s) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
   s->launches += 1;
+  s->herm_ok = true;
+  s->lower_stale = false;
   return cuda_fail(s, launch_init_zero_state(s->rho, s->n, s->prec, s->stream));
 }
 
 tq_status tq_rho_device_ptr(tq_state* s, void** out) {
   if (!s || !out) return TQ_ERR_ARG;
+  if (s->lower_stale && !s->poisoned) {
+    s->launches += 1;
+    tq_status st = cuda_fail(s, launch_mirror_lower(static_cast<double2*>(s->rho), s->n, s->stream));
+    if (st != TQ_OK) return st;
+    s->lower_stale = false;
+  }
   *out = s->rho;
+  return TQ_OK;
+}
+
+tq_status tq_set_hermitian(tq_state* s, int on) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (!on && s->lower_stale) {
+    s->launches += 1;
+    st = cuda_fail(s, launch_mirror_lower(static_cast<double2*>(s->rho), s->n, s->stream));
+    if (st != TQ_OK) return st;
+    s->lower_stale = false;
+  }
+  s->herm_mode = on != 0;
+  return TQ_OK;
+}
+
+tq_status tq_is_hermitian_mode(const tq_state* s, int* active) {
+  if (!s || !active) return TQ_ERR_ARG;
+  *active = (s->prec == TQ_FP64 && s->herm_mode && s->herm_ok) ? 1 : 0;
   return TQ_OK;
 }
 
@@ -481,6 +523,8 @@ tq_status tq_get_rho(tq_state* s, double* out) {
   const size_t entries = 1ull << (2 * s->n);
   cudaError_t e;
   if (s->prec == TQ_FP64) {
+    void* full = nullptr;
+    if ((st = tq_rho_device_ptr(s, &full)) != TQ_OK) return st;  // fills the lower triangle if needed
     e = cudaMemcpyAsync(out, s->rho, entries * 16, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return cuda_fail(s, e);
@@ -508,8 +552,20 @@ tq_status tq_set_rho(tq_state* s, const double* in) {
   cudaError_t e;
   if (s->prec == TQ_FP64) {
     e = cudaMemcpyAsync(s->rho, in, entries * 16, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    // Hermitian mode stays on only if the new rho is Hermitian to rounding
+    if ((st = ensure(s, s->red, kRedBytes)) != TQ_OK) return st;
+    if ((st = ensure_pinned(s, s->pin_small, 4096)) != TQ_OK) return st;
+    double* dres = reinterpret_cast<double*>(static_cast<char*>(s->red.ptr) + kRedOut);
+    double* hres = static_cast<double*>(s->pin_small.ptr) + 64;
+    e = launch_hermiticity(static_cast<const double2*>(s->rho), s->n, dres, s->stream);
+    s->launches += 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hres, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return cuda_fail(s, e);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    s->herm_ok = hres[0] <= 4.0 * 2.220446049250313e-16 * hres[1];
+    s->lower_stale = false;
+    return TQ_OK;
   }
   const size_t chunk = std::min<size_t>(entries, 1ull << 22);
   if ((st = ensure(s, s->staging, chunk * 16)) != TQ_OK) return st;

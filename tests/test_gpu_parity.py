@@ -230,6 +230,7 @@ def _factorised_check(tq, n, subset, width, precision, n_gates, seed, n_samples=
     with tq.State(n, precision) as st:
         st.run(prefix + body, width=width)
         tr = st.trace()
+        st.device_ptr()                                  # every entry current (Hermitian mode)
         vec = st._buf.view(torch.complex128 if precision == "fp64" else torch.complex64)
         N = 1 << n
         rng = np.random.default_rng(seed)
@@ -303,8 +304,11 @@ def test_profile_counts_launches(tq):
     assert stats["apply_f64_w2"]["launches"] == nb
     assert stats["superop_build"]["launches"] == 1 and stats["fuse"]["launches"] == 1
     assert stats["reduce"]["launches"] == 2
-    assert stats["apply_f64_w2"]["flops"] == 8.0 * 4 ** n * 16
-    assert stats["apply_f64_w2"]["bytes"] == 2 * 16 * 4 ** n
+    # Hermitian mode computes the canonical groups only: M (M + 1) / 2 of M^2
+    M = 2 ** (n - 2)
+    groups = M * (M + 1) // 2
+    assert stats["apply_f64_w2"]["flops"] == 8.0 * groups * 16 * 16
+    assert stats["apply_f64_w2"]["bytes"] == 2 * 16 * groups * 16
     assert all(v["total_ms"] > 0 for v in stats.values())
 
 
@@ -321,6 +325,7 @@ def test_layered_thermal_12q_fusion_widths_agree(tq):
             nb = st.run(c.ops, width=width)
             z = st.expect_z(masks)
             tr = st.trace()
+            st.device_ptr()
             v = st._buf.view(torch.complex128)[idx].cpu().numpy()
         assert abs(tr - 1) < 1e-11
         if ref is None:
@@ -329,3 +334,39 @@ def test_layered_thermal_12q_fusion_widths_agree(tq):
         assert nb < ref[2]
         assert maxabs(z, ref[0]) < TOL64, width
         assert maxabs(v, ref[1]) < TOL64, width
+
+
+@pytest.mark.parametrize("width", [0, 1, 2, 3, 4])
+def test_hermitian_mode_matches_full_update_and_oracle(tq, width):
+    n = 7
+    c = W.random_noisy_circuit(n, 80, 61 + width, gate_set=("h", "s", "rx", "cx", "su2", "rzz"))
+    want = O.run_circuit(n, c.ops)
+    with tq.State(n, "fp64") as a, tq.State(n, "fp64", hermitian=False) as b:
+        assert a.hermitian_mode() and not b.hermitian_mode()
+        a.run(c.ops, width=width)
+        b.run(c.ops, width=width)
+        ra, rb = a.rho(), b.rho()
+        za, zb = a.expect_z([1, 6, 127]), b.expect_z([1, 6, 127])
+    assert maxabs(ra, want) < TOL64 and maxabs(rb, want) < TOL64
+    off = ~np.eye(1 << n, dtype=bool)                   # the lower triangle mirrors the upper exactly;
+    assert np.array_equal(ra[off], ra.conj().T[off])    # the diagonal keeps rounding-level Im parts
+    assert np.max(np.abs(np.diag(ra).imag)) < 1e-15
+    assert maxabs(za, zb) < TOL64
+
+
+def test_hermitian_mode_follows_set_rho(tq):
+    n = 5
+    with tq.State(n, "fp64") as st:
+        st.set_rho(random_general_matrix(n, 3))         # not Hermitian: full updates
+        assert not st.hermitian_mode()
+        herm = W.random_density_matrix(n, 4)
+        herm = 0.5 * (herm + herm.conj().T)
+        st.set_rho(herm)
+        assert st.hermitian_mode()
+        st.run([("cx", [0, 3], ()), ("depol", [0, 3], (0.1,))], width=2)
+        assert maxabs(st.rho(), O.run_circuit(n, [("cx", [0, 3], ()), ("depol", [0, 3], (0.1,))], herm)) < TOL64
+        st.set_hermitian(False)                          # fills the lower half, then full updates
+        assert not st.hermitian_mode()
+        st.reset()
+        st.set_hermitian(True)
+        assert st.hermitian_mode()
