@@ -413,6 +413,14 @@ tq_status tq_plan_fusion(int n_qubits, const tq_op* ops, size_t n_ops, int max_f
                          int precision, int* block_of_op, int* block_width,
                          size_t* n_blocks_out);
 
+/* Structural nonzero pattern of an op's superoperator (ops on 1 or 2
+ * qubits; TQ_ERR_UNSUPPORTED otherwise): *width_out = k, *nnz_out = number of
+ * entries S[i][j] that may be nonzero, rows_out[i] (if not NULL, 4^k
+ * entries) = bit mask of the columns j of row i. Depolarising channels give
+ * their exact pattern. FP64 fused blocks of width <= 2 with at most 75%
+ * nonzeros are applied from row lists (exact zeros skipped). */
+tq_status tq_op_pattern(const tq_op* op, int* width_out, int* nnz_out, uint16_t* rows_out);
+
 /* Base vec index of group g for a block whose 2k target bit positions are
  * positions[0..2k-1] (any order): g with a zero bit inserted at every target
  * position, in increasing position order. For k = 1 and positions (q, q+n)

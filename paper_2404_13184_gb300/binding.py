@@ -100,6 +100,7 @@ _SIGNATURES = [
     ("tq_plan_fusion", c_int, [c_int, POINTER(TqOp), c_size_t, c_int, c_int, POINTER(c_int), POINTER(c_int),
                                POINTER(c_size_t)]),
     ("tq_group_base", c_uint64, [c_uint64, POINTER(c_int), c_int]),
+    ("tq_op_pattern", c_int, [POINTER(TqOp), POINTER(c_int), POINTER(c_int), POINTER(ctypes.c_uint16)]),
     ("tq_status_string", ctypes.c_char_p, [c_int]),
     ("tq_version", ctypes.c_char_p, []),
 ]
@@ -362,6 +363,17 @@ def expect_z_noalloc(rho_dev_ptr: int, n: int, precision: str, masks_dev_ptr: in
     lib = load()
     _check(lib.tq_expect_z_noalloc(c_void_p(rho_dev_ptr), n, PRECISION[precision], c_void_p(masks_dev_ptr), n_masks,
                                    c_void_p(out_dev_ptr), c_void_p(stream)), "tq_expect_z_noalloc")
+
+
+def op_pattern(op) -> np.ndarray:
+    """Boolean 4^k x 4^k structural pattern of an op's superoperator."""
+    lib = load()
+    prog = Program([op])
+    w, nnz = c_int(0), c_int(0)
+    rows = (ctypes.c_uint16 * 16)()
+    _check(lib.tq_op_pattern(prog.arr, ctypes.byref(w), ctypes.byref(nnz), rows), "tq_op_pattern")
+    D = 1 << (2 * w.value)
+    return np.array([[(rows[i] >> j) & 1 for j in range(D)] for i in range(D)], dtype=bool)
 
 
 def group_base(g: int, positions) -> int:

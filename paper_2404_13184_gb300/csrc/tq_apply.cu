@@ -144,6 +144,85 @@ __global__ void __launch_bounds__(256) k_apply_direct_herm(T2* rho, const T2* __
   apply_direct_body<T2, K, true>(rho, S, p);
 }
 
+// Sparse FP64 blocks (width <= 2): the row lists sit in shared memory and a
+// thread's group entries in its own shared-memory column (slot l at
+// sX[l * 256 + thread]), so a row costs one broadcast entry load, one
+// conflict-free slot load and four DFMA per nonzero.
+template <int K, bool HERM>
+__global__ void __launch_bounds__(256) k_apply_sparse(double2* rho, const SparseBlock* __restrict__ sp,
+                                                      const __grid_constant__ ApplyParams p) {
+  constexpr int D = 1 << (2 * K);
+  __shared__ int s_rowptr[D + 1];
+  __shared__ double2 s_v[D * D];
+  __shared__ int s_col[D * D];
+  extern __shared__ __align__(16) double2 sX[];
+  if (threadIdx.x <= D) s_rowptr[threadIdx.x] = sp->rowptr[threadIdx.x];
+  __syncthreads();
+  for (int k = threadIdx.x; k < s_rowptr[D]; k += blockDim.x) {
+    s_v[k] = sp->e[k].v;
+    s_col[k] = sp->e[k].col;
+  }
+  __syncthreads();
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long total = HERM ? p.n_canon : p.n_groups;
+  const unsigned long long rmask = (1ull << p.n) - 1ull;
+  double2* mine = sX + threadIdx.x;
+  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total; t += stride) {
+    bool self = false;
+    unsigned long long base = HERM ? canonical_group(t, p.n - K, &self) : t;
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) {
+      const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
+      base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
+    }
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      const unsigned long long e = base + p.off[l];
+      double2 v;
+      if (!HERM) {
+        v = rho[e];
+      } else {
+        const unsigned long long r = e & rmask, c = e >> p.n;
+        v = rho[r <= c ? e : (c | (r << p.n))];
+        if (r > c) v.y = -v.y;
+      }
+      mine[l * 256] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = s_rowptr[i]; k < s_rowptr[i + 1]; ++k)
+        CplxOps<double2>::fma(acc, s_v[k], mine[s_col[k] * 256]);
+      const unsigned long long e = base + p.off[i];
+      if (!HERM) {
+        rho[e] = acc;
+      } else {
+        const unsigned long long r = e & rmask, c = e >> p.n;
+        if (r <= c) {
+          rho[e] = acc;
+        } else if (!self) {
+          acc.y = -acc.y;
+          rho[c | (r << p.n)] = acc;
+        }
+      }
+    }
+  }
+}
+
+template <int K, bool HERM>
+cudaError_t run_sparse(double2* rho, const SparseBlock* sp, const ApplyParams& p, int num_sms, cudaStream_t st) {
+  constexpr int D = 1 << (2 * K);
+  const size_t smem = (size_t)D * 256 * sizeof(double2);
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute(k_apply_sparse<K, HERM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  const unsigned long long blocks = ((HERM ? p.n_canon : p.n_groups) + 255) / 256;
+  const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(blocks, (unsigned long long)num_sms * 8));
+  k_apply_sparse<K, HERM><<<grid, 256, smem, st>>>(rho, sp, p);
+  return cudaGetLastError();
+}
+
 // Widths 3 and 4: a CTA stages the entries of G consecutive groups (4^K x G)
 // in shared memory, then thread (rowset, gi) computes rows i = rowset +
 // (256/G) r of group gi and writes them straight back to global memory (the
@@ -276,10 +355,15 @@ cudaError_t run_direct(T2* rho, const T2* S, const ApplyParams& p, int num_sms, 
 }  // namespace
 
 cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyParams& p, int num_sms,
-                         cudaStream_t st) {
+                         cudaStream_t st, const SparseBlock* sparse) {
   if (precision == 0) {
     double2* r = static_cast<double2*>(rho);
     const double2* s = static_cast<const double2*>(S);
+    if (p.sparse && sparse && p.width <= 2) {
+      if (p.herm)
+        return p.width == 1 ? run_sparse<1, true>(r, sparse, p, num_sms, st) : run_sparse<2, true>(r, sparse, p, num_sms, st);
+      return p.width == 1 ? run_sparse<1, false>(r, sparse, p, num_sms, st) : run_sparse<2, false>(r, sparse, p, num_sms, st);
+    }
     if (p.herm) {
       switch (p.width) {
         case 1: return run_direct<double2, 1, true>(r, s, p, num_sms, st);

@@ -57,8 +57,27 @@ struct ApplyParams {
   // canonical groups (row rest a <= column rest b, n_canon of them) and
   // storing only entries with row <= column (see tq_apply.cu).
   int herm;
-  int pad;
+  int sparse;  // FP64 blocks of width <= 2: apply from the block's row lists
   unsigned long long n_canon;
+};
+
+// Row lists of a sparse FP64 superoperator (width <= 2, D <= 16): the
+// nonzeros of row i are e[rowptr[i] .. rowptr[i+1]).
+struct SparseEntry {
+  double2 v;
+  int col;
+  int pad[3];
+};
+struct SparseBlock {
+  int rowptr[17];
+  int pad[15];
+  SparseEntry e[256];
+};
+
+// Work item of the sparse compression: block index and its row-list slot.
+struct SparseWork {
+  int block;
+  int slot;
 };
 
 // Group index of the t-th canonical group (a <= b, enumerated column by
@@ -91,6 +110,10 @@ cudaError_t launch_fuse(const double2* sops, const OpDesc* ops, const BlockDesc*
                         const MemberDesc* members, const FuseWork* work, int n_work,
                         double2* sb64, float2* sb32, cudaStream_t st);
 cudaError_t launch_init_zero_state(void* rho, int n, int precision, cudaStream_t st);
+// Row lists (exact zeros dropped) of the fused FP64 superoperators of the
+// listed blocks.
+cudaError_t launch_compress_sparse(const double2* sb64, const BlockDesc* blocks, const SparseWork* work, int n_work,
+                                   SparseBlock* out, cudaStream_t st);
 // Reductions over the diagonal: quantities [Re tr, Im tr, Re Tr(rho Z_mask_i)...]
 // partials: gridDim x nq doubles of scratch; out: nq doubles (device).
 int diag_reduce_grid(int n);
@@ -112,6 +135,6 @@ cudaError_t launch_hermiticity(const double2* rho, int n, double* out, cudaStrea
 // One pass of a fused block over vec(rho). S: 4^K x 4^K superoperator,
 // row-major (double2 for FP64 states, float2 for split states).
 cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyParams& p,
-                         int num_sms, cudaStream_t st);
+                         int num_sms, cudaStream_t st, const SparseBlock* sparse = nullptr);
 
 }  // namespace tq

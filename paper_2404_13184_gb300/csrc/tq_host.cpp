@@ -96,29 +96,144 @@ tq_status resolve_op(const tq_op& op, ResolvedOp* out) {
   return TQ_ERR_ARG;
 }
 
-double block_cost(int width, int precision) {
+namespace {
+
+// Index helpers for patterns: local index l = r + d c (d = 2^w), with bit j
+// of r and of c for local qubit j.
+int op_index(int i, const int* pos, int k, int W) {
+  int r = 0, c = 0;
+  for (int j = 0; j < k; ++j) {
+    r |= ((i >> pos[j]) & 1) << j;
+    c |= ((i >> (pos[j] + W)) & 1) << j;
+  }
+  return r | (c << k);
+}
+
+int rest_of(int i, const int* pos, int k, int W) {
+  int m = 0;
+  for (int j = 0; j < k; ++j) m |= (1 << pos[j]) | (1 << (pos[j] + W));
+  return i & ~m;
+}
+
+// Pattern p (width k) placed at block positions pos[0..k-1] of a width-W block.
+Pattern embed(const Pattern& p, const int* pos, int W) {
+  Pattern o;
+  o.width = W;
+  const int D = 1 << (2 * W);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j)
+      if (rest_of(i, pos, p.width, W) == rest_of(j, pos, p.width, W) &&
+          ((p.row[op_index(i, pos, p.width, W)] >> op_index(j, pos, p.width, W)) & 1))
+        o.row[i] |= (uint16_t)(1u << j);
+  return o;
+}
+
+// later x earlier (both of the same width)
+Pattern compose(const Pattern& later, const Pattern& earlier) {
+  Pattern o;
+  o.width = later.width;
+  const int D = 1 << (2 * later.width);
+  for (int i = 0; i < D; ++i)
+    for (int m = 0; m < D; ++m)
+      if ((later.row[i] >> m) & 1) o.row[i] |= earlier.row[m];
+  return o;
+}
+
+}  // namespace
+
+int pattern_nnz(const Pattern& p) {
+  int c = 0;
+  for (int i = 0; i < (1 << (2 * p.width)); ++i) c += __builtin_popcount(p.row[i]);
+  return c;
+}
+
+bool op_pattern(const tq_op& op, const ResolvedOp& r, Pattern* out) {
+  if (r.k > 2) return false;
+  Pattern p;
+  p.width = r.k;
+  const int d = 1 << r.k, D = d * d;
+  const bool depol = op.kind == TQ_OP_CHANNEL && op.name == TQ_CH_DEPOLARIZING;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      const int rp = i % d, cp = i / d, rr = j % d, cc = j / d;
+      bool nz = false;
+      if (depol) {
+        nz = (rp == cp && rr == cc) || (rp == rr && cp == cc);
+      } else {
+        for (int t = 0; t < r.m && !nz; ++t) {
+          const cplx* K = r.kraus.data() + (size_t)t * d * d;
+          nz = K[rp * d + rr] != cplx(0.0, 0.0) && K[cp * d + cc] != cplx(0.0, 0.0);
+        }
+      }
+      if (nz) p.row[i] |= (uint16_t)(1u << j);
+    }
+  *out = p;
+  return true;
+}
+
+bool block_is_sparse(const Block& b, int precision) {
+  if (precision != TQ_FP64 || !b.has_pat || b.width > 2) return false;
+  const int D = 1 << (2 * b.width);
+  return pattern_nnz(b.pat) <= kSparseFraction * D * D;
+}
+
+double block_cost(int width, int precision, int nnz) {
   // Time of one pass over all 4^n entries, relative units, from the measured
   // GB300 rates: HBM ~6.8 TB/s, DFMA ~1.2 TFLOP/s, FFMA ~74 TFLOP/s.
-  // A width-k pass moves 2*B bytes and does 8*4^k flops per entry.
+  // A width-k pass moves 2*B bytes per entry and does 8*4^k flops per entry
+  // (dense), or 8 * nnz / 4^k with a sparse FP64 superoperator.
   const double hbm = 6.8e12, dfma = 1.2e12, ffma = 74e12;
   const double bytes = precision == TQ_FP64 ? 32.0 : 16.0;
-  const double flops = 8.0 * std::pow(4.0, width);
+  const int D = 1 << (2 * width);
+  const bool sparse = precision == TQ_FP64 && width <= 2 && nnz >= 0 && nnz <= kSparseFraction * D * D;
+  const double flops = sparse ? 8.0 * nnz / D : 8.0 * D;
   const double pipe = precision == TQ_FP64 ? dfma : ffma;
   return std::max(bytes / hbm, flops / pipe) * 1e12;
 }
 
-tq_status plan_fusion(int n, const std::vector<std::vector<int>>& op_qubits, int max_width,
-                      int precision, std::vector<Block>* blocks) {
+namespace {
+
+double cost_of(const Block& b, int precision) {
+  return block_cost(b.width, precision, b.has_pat ? pattern_nnz(b.pat) : -1);
+}
+
+// The block B extended by op: its qubit list and (if both have patterns and
+// the result is at most 2 wide) its pattern.
+Block extended(const Block& B, const PlanOp& op) {
+  Block X;
+  X.width = B.width;
+  for (int j = 0; j < B.width; ++j) X.qubits[j] = B.qubits[j];
+  for (int v : op.qubits)
+    if (std::find(X.qubits, X.qubits + X.width, v) == X.qubits + X.width) {
+      if (X.width < 4) X.qubits[X.width] = v;
+      ++X.width;
+    }
+  X.has_pat = X.width <= 2 && op.has_pat && (B.has_pat || B.ops.empty());
+  if (X.has_pat) {
+    int pos_b[2] = {0, 1}, pos_o[2] = {0, 0};
+    for (size_t j = 0; j < op.qubits.size(); ++j)
+      pos_o[j] = (int)(std::find(X.qubits, X.qubits + X.width, op.qubits[j]) - X.qubits);
+    const Pattern po = embed(op.pat, pos_o, X.width);
+    X.pat = B.ops.empty() ? po : compose(po, embed(B.pat, pos_b, X.width));
+  }
+  return X;
+}
+
+}  // namespace
+
+tq_status plan_fusion(int n, const std::vector<PlanOp>& ops, int max_width, int precision,
+                      std::vector<Block>* blocks) {
   blocks->clear();
   if (max_width < -1 || max_width > kMaxWidth) return TQ_ERR_ARG;
   const bool automatic = max_width == -1;
   const int cap = automatic ? kMaxWidth : max_width;
   // last block index that touched each qubit
   std::vector<int> last(n, -1);
-  for (size_t i = 0; i < op_qubits.size(); ++i) {
-    const std::vector<int>& q = op_qubits[i];
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const std::vector<int>& q = ops[i].qubits;
     const int k = (int)q.size();
     int chosen = -1;
+    Block chosen_ext;
     if (max_width != 0 && k <= cap) {
       int barrier = -1;
       for (int v : q) barrier = std::max(barrier, last[v]);
@@ -130,32 +245,33 @@ tq_status plan_fusion(int n, const std::vector<std::vector<int>>& op_qubits, int
       double best_delta = 1e300;
       for (int b = (int)blocks->size() - 1; b >= lo; --b) {
         const Block& B = (*blocks)[b];
-        int w = B.width;
-        for (int v : q)
-          if (std::find(B.qubits, B.qubits + B.width, v) == B.qubits + B.width) ++w;
-        if (w > cap) continue;
-        const double delta = automatic
-                                 ? block_cost(w, precision) - block_cost(B.width, precision)
-                                 : (double)(w - B.width);
+        Block X = extended(B, ops[i]);
+        if (X.width > cap) continue;
+        const double delta = automatic ? cost_of(X, precision) - cost_of(B, precision) : (double)(X.width - B.width);
         if (delta < best_delta - 1e-9) {
           best_delta = delta;
           chosen = b;
+          chosen_ext = X;
         }
       }
       // automatic mode merges only when that is no dearer than a pass of its own
-      if (automatic && chosen >= 0 && best_delta > block_cost(k, precision) * (1 + 1e-9)) chosen = -1;
+      if (automatic && chosen >= 0) {
+        Block alone = extended(Block(), ops[i]);
+        if (best_delta > cost_of(alone, precision) * (1 + 1e-9)) chosen = -1;
+      }
     }
     if (chosen < 0) {
-      Block B;
-      B.width = 0;
-      blocks->push_back(B);
+      blocks->push_back(extended(Block(), ops[i]));
       chosen = (int)blocks->size() - 1;
+    } else {
+      Block& B = (*blocks)[chosen];
+      B.width = chosen_ext.width;
+      for (int j = 0; j < 4; ++j) B.qubits[j] = chosen_ext.qubits[j];
+      B.has_pat = chosen_ext.has_pat;
+      B.pat = chosen_ext.pat;
     }
     Block& B = (*blocks)[chosen];
-    for (int v : q) {
-      if (std::find(B.qubits, B.qubits + B.width, v) == B.qubits + B.width) B.qubits[B.width++] = v;
-      last[v] = std::max(last[v], chosen);
-    }
+    for (int v : q) last[v] = std::max(last[v], chosen);
     B.ops.push_back((int)i);
   }
   return TQ_OK;
@@ -349,14 +465,17 @@ tq_status tq_plan_fusion(int n, const tq_op* ops, size_t n_ops, int max_width, i
                          int* block_of_op, int* block_width, size_t* n_blocks_out) {
   if (n < 1 || n > kMaxQubits || (!ops && n_ops) || !n_blocks_out) return TQ_ERR_ARG;
   if (precision != TQ_FP64 && precision != TQ_SPLIT) return TQ_ERR_ARG;
-  std::vector<std::vector<int>> qs(n_ops);
+  std::vector<PlanOp> pops(n_ops);
   for (size_t i = 0; i < n_ops; ++i) {
     tq_status st = validate_op(n, ops[i]);
     if (st != TQ_OK) return st;
-    qs[i].assign(ops[i].qubits, ops[i].qubits + ops[i].k);
+    ResolvedOp r;
+    if ((st = resolve_op(ops[i], &r)) != TQ_OK) return st;
+    pops[i].qubits.assign(ops[i].qubits, ops[i].qubits + ops[i].k);
+    pops[i].has_pat = op_pattern(ops[i], r, &pops[i].pat);
   }
   std::vector<Block> blocks;
-  tq_status st = plan_fusion(n, qs, max_width, precision, &blocks);
+  tq_status st = plan_fusion(n, pops, max_width, precision, &blocks);
   if (st != TQ_OK) return st;
   for (size_t b = 0; b < blocks.size(); ++b) {
     for (int i : blocks[b].ops)
@@ -364,6 +483,21 @@ tq_status tq_plan_fusion(int n, const tq_op* ops, size_t n_ops, int max_width, i
     if (block_width) block_width[b] = blocks[b].width;
   }
   *n_blocks_out = blocks.size();
+  return TQ_OK;
+}
+
+tq_status tq_op_pattern(const tq_op* op, int* width_out, int* nnz_out, uint16_t* rows_out) {
+  if (!op || !width_out || !nnz_out) return TQ_ERR_ARG;
+  tq_status st = validate_op(kMaxQubits, *op);
+  if (st != TQ_OK) return st;
+  ResolvedOp r;
+  if ((st = resolve_op(*op, &r)) != TQ_OK) return st;
+  Pattern p;
+  if (!op_pattern(*op, r, &p)) return TQ_ERR_UNSUPPORTED;
+  *width_out = p.width;
+  *nnz_out = pattern_nnz(p);
+  if (rows_out)
+    for (int i = 0; i < (1 << (2 * p.width)); ++i) rows_out[i] = p.row[i];
   return TQ_OK;
 }
 

@@ -23,13 +23,41 @@ struct ResolvedOp {
   int m = 0;
 };
 
+// Structural nonzero pattern of a superoperator on at most 2 qubits
+// (D = 4^width <= 16 local indices): bit j of row[i] is set when S[i][j]
+// may be nonzero. Used only for planning and kernel choice.
+struct Pattern {
+  int width = 0;
+  uint16_t row[16] = {};
+};
+
 // One fused block: an ordered qubit list (local bit j = qubits[j]) and the
-// ops it composes, in circuit order.
+// ops it composes, in circuit order. has_pat: pat is the block's pattern
+// (blocks of at most 2 qubits whose ops all have patterns).
 struct Block {
   int width = 0;
   int qubits[4] = {0, 0, 0, 0};
   std::vector<int> ops;
+  bool has_pat = false;
+  Pattern pat;
 };
+
+// An op as the planner sees it.
+struct PlanOp {
+  std::vector<int> qubits;
+  bool has_pat = false;
+  Pattern pat;
+};
+
+// Structural pattern of an op's superoperator S = sum conj(K) (x) K (ops on
+// at most 2 qubits; false otherwise). Depolarising channels use their exact
+// pattern (the X and Y Pauli terms cancel on coherence-to-coherence entries).
+bool op_pattern(const tq_op& op, const ResolvedOp& r, Pattern* out);
+int pattern_nnz(const Pattern& p);
+// Sparse apply kernels are used for FP64 blocks of width <= 2 whose pattern
+// has at most this fraction of nonzeros.
+constexpr double kSparseFraction = 0.75;
+bool block_is_sparse(const Block& b, int precision);
 
 // Validate an op against n qubits (qubit range, distinctness, k, m, mats).
 tq_status validate_op(int n, const tq_op& op);
@@ -38,12 +66,13 @@ tq_status validate_op(int n, const tq_op& op);
 tq_status resolve_op(const tq_op& op, ResolvedOp* out);
 
 // Per-precision cost (arbitrary units per 4^n entries) of one apply pass of
-// a block of the given width; used by the automatic fusion planner.
-double block_cost(int width, int precision);
+// a block of the given width; nnz < 0 means dense. Used by the automatic
+// fusion planner.
+double block_cost(int width, int precision, int nnz = -1);
 
 // Greedy fusion planner (Sec. 3.3, generalised to blocks of <= max_width
 // qubits). max_width 0: one block per op; -1: automatic (cost model).
-tq_status plan_fusion(int n, const std::vector<std::vector<int>>& op_qubits, int max_width,
-                      int precision, std::vector<Block>* blocks);
+tq_status plan_fusion(int n, const std::vector<PlanOp>& ops, int max_width, int precision,
+                      std::vector<Block>* blocks);
 
 }  // namespace tq

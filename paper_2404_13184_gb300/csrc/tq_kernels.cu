@@ -114,6 +114,48 @@ __global__ void __launch_bounds__(256) k_fuse(const double2* __restrict__ sops,
   }
 }
 
+// One CTA per sparse block: row i's nonzeros (exactly zero entries of the
+// fused FP64 superoperator are dropped) in column order.
+__global__ void k_compress_sparse(const double2* __restrict__ sb64, const BlockDesc* __restrict__ blocks,
+                                  const SparseWork* __restrict__ work, SparseBlock* __restrict__ out) {
+  __shared__ int cnt[16];
+  const SparseWork w = work[blockIdx.x];
+  const BlockDesc b = blocks[w.block];
+  const int D = 1 << (2 * b.width);
+  const double2* S = sb64 + b.sb_off;
+  SparseBlock* o = out + w.slot;
+  const int i = threadIdx.x;
+  if (i < D) {
+    int c = 0;
+    for (int j = 0; j < D; ++j) {
+      const double2 v = S[i * D + j];
+      c += (v.x != 0.0 || v.y != 0.0) ? 1 : 0;
+    }
+    cnt[i] = c;
+  }
+  __syncthreads();
+  if (i == 0) {
+    int acc = 0;
+    for (int r = 0; r < D; ++r) {
+      o->rowptr[r] = acc;
+      acc += cnt[r];
+    }
+    o->rowptr[D] = acc;
+  }
+  __syncthreads();
+  if (i < D) {
+    int k = o->rowptr[i];
+    for (int j = 0; j < D; ++j) {
+      const double2 v = S[i * D + j];
+      if (v.x != 0.0 || v.y != 0.0) {
+        o->e[k].v = v;
+        o->e[k].col = j;
+        ++k;
+      }
+    }
+  }
+}
+
 __global__ void k_set_one(void* rho, int precision) {
   if (precision == 0)
     reinterpret_cast<double2*>(rho)[0] = make_double2(1.0, 0.0);
@@ -264,6 +306,13 @@ cudaError_t launch_fuse(const double2* sops, const OpDesc* ops, const BlockDesc*
                         float2* sb32, cudaStream_t st) {
   if (n_work <= 0) return cudaSuccess;
   k_fuse<<<n_work, 256, 0, st>>>(sops, ops, blocks, members, work, sb64, sb32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compress_sparse(const double2* sb64, const BlockDesc* blocks, const SparseWork* work, int n_work,
+                                   SparseBlock* out, cudaStream_t st) {
+  if (n_work <= 0) return cudaSuccess;
+  k_compress_sparse<<<n_work, 32, 0, st>>>(sb64, blocks, work, out);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ struct HostTables {
   std::vector<BlockDesc> blocks;
   std::vector<MemberDesc> members;
   std::vector<FuseWork> work;
+  std::vector<SparseWork> spw;  // blocks applied from row lists (FP64)
   long long sop_entries = 0;
   long long sb_entries = 0;
 };
@@ -46,9 +47,12 @@ struct tq_program {
   int n_work = 0;
   std::vector<tq::ApplyParams> params;  // per block
   std::vector<long long> sb_off;    // per block, complex entries
+  std::vector<int> sp_slot;         // per block: row-list slot, or -1 (dense)
+  std::vector<int> nnz;             // per block: structural nonzeros (D*D if dense)
+  int n_sparse = 0;
   // device tables (one blob: Kraus sets, op/block/member/work tables)
-  tq::DevBuf blob, sops, sb64, sb32;
-  size_t o_kraus = 0, o_ops = 0, o_blk = 0, o_mem = 0, o_work = 0, blob_bytes = 0;
+  tq::DevBuf blob, sops, sb64, sb32, sps;
+  size_t o_kraus = 0, o_ops = 0, o_blk = 0, o_mem = 0, o_work = 0, o_spw = 0, blob_bytes = 0;
   bool owns = true;  // standalone programs own their buffers
 };
 

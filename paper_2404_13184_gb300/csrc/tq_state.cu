@@ -17,10 +17,14 @@ namespace {
 
 
 // Kernel kinds for launch counting and event profiling.
-enum Kind { K_BUILD = 0, K_FUSE, K_REDUCE, K_APPLY64 /* +w-1 */, K_APPLY32 = K_APPLY64 + 4, K_NKINDS = K_APPLY32 + 4 };
-const char* kKindName[K_NKINDS] = {"superop_build", "fuse",         "reduce",       "apply_f64_w1",
-                                   "apply_f64_w2",  "apply_f64_w3", "apply_f64_w4", "apply_f32_w1",
-                                   "apply_f32_w2",  "apply_f32_w3", "apply_f32_w4"};
+enum Kind {
+  K_BUILD = 0, K_FUSE, K_REDUCE, K_APPLY64 /* +w-1 */, K_APPLY32 = K_APPLY64 + 4, K_PACK = K_APPLY32 + 4,
+  K_SPARSE64 /* +w-1 */, K_NKINDS = K_SPARSE64 + 2
+};
+const char* kKindName[K_NKINDS] = {"superop_build", "fuse",         "reduce",        "apply_f64_w1",
+                                   "apply_f64_w2",  "apply_f64_w3", "apply_f64_w4",  "apply_f32_w1",
+                                   "apply_f32_w2",  "apply_f32_w3", "apply_f32_w4",  "sparse_pack",
+                                   "apply_f64_sparse_w1", "apply_f64_sparse_w2"};
 
 struct Pending {
   int kind;
@@ -196,7 +200,7 @@ ApplyParams apply_params(int n, const Block& B) {
 // Validate, resolve and plan `ops` into P's host fields and `t`.
 tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t) {
   if (width < -1 || width > kMaxWidth) return TQ_ERR_ARG;
-  std::vector<std::vector<int>> qs(n_ops);
+  std::vector<PlanOp> qs(n_ops);
   t->ops.resize(n_ops);
   P->max_dim2 = 0;
   for (size_t i = 0; i < n_ops; ++i) {
@@ -205,7 +209,8 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
     ResolvedOp r;
     st = resolve_op(ops[i], &r);
     if (st != TQ_OK) return st;
-    qs[i].assign(ops[i].qubits, ops[i].qubits + ops[i].k);
+    qs[i].qubits.assign(ops[i].qubits, ops[i].qubits + ops[i].k);
+    qs[i].has_pat = op_pattern(ops[i], r, &qs[i].pat);
     OpDesc& od = t->ops[i];
     od.k = r.k;
     od.m = r.m;
@@ -225,6 +230,9 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
   P->max_width = 0;
   P->params.clear();
   P->sb_off.clear();
+  P->sp_slot.clear();
+  P->nnz.clear();
+  P->n_sparse = 0;
   for (size_t b = 0; b < plan.size(); ++b) {
     const Block& B = plan[b];
     BlockDesc bd{};
@@ -245,7 +253,16 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
     t->blocks.push_back(bd);
     const int C = std::min(D, 1024 / D);
     for (int c0 = 0; c0 < D; c0 += C) t->work.push_back(FuseWork{(int)b, c0});
-    P->params.push_back(apply_params(n, B));
+    ApplyParams ap = apply_params(n, B);
+    P->nnz.push_back(B.has_pat ? pattern_nnz(B.pat) : D * D);
+    if (block_is_sparse(B, prec)) {
+      ap.sparse = 1;
+      t->spw.push_back(SparseWork{(int)b, P->n_sparse});
+      P->sp_slot.push_back(P->n_sparse++);
+    } else {
+      P->sp_slot.push_back(-1);
+    }
+    P->params.push_back(ap);
     P->sb_off.push_back(bd.sb_off);
     P->max_width = std::max(P->max_width, B.width);
   }
@@ -256,6 +273,7 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
   P->o_blk = off;   off = align_up(off + t->blocks.size() * sizeof(BlockDesc), 256);
   P->o_mem = off;   off = align_up(off + t->members.size() * sizeof(MemberDesc), 256);
   P->o_work = off;  off = align_up(off + t->work.size() * sizeof(FuseWork), 256);
+  P->o_spw = off;   off = align_up(off + t->spw.size() * sizeof(SparseWork), 256);
   P->blob_bytes = std::max<size_t>(off, 256);
   return TQ_OK;
 }
@@ -266,6 +284,7 @@ void pack_blob(const tq_program& P, const HostTables& t, char* h) {
   std::memcpy(h + P.o_blk, t.blocks.data(), t.blocks.size() * sizeof(BlockDesc));
   std::memcpy(h + P.o_mem, t.members.data(), t.members.size() * sizeof(MemberDesc));
   std::memcpy(h + P.o_work, t.work.data(), t.work.size() * sizeof(FuseWork));
+  if (!t.spw.empty()) std::memcpy(h + P.o_spw, t.spw.data(), t.spw.size() * sizeof(SparseWork));
 }
 
 }  // namespace tq
@@ -289,6 +308,12 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
   });
   if (e == cudaSuccess)
     e = timed(s, K_FUSE, 1, [&] { return launch_fuse(sops, d_ops, d_blk, d_mem, d_work, P.n_work, sb64, sb32, s->stream); });
+  SparseBlock* sps = static_cast<SparseBlock*>(P.sps.ptr);
+  if (e == cudaSuccess && P.n_sparse > 0)
+    e = timed(s, K_PACK, 1, [&] {
+      return launch_compress_sparse(sb64, d_blk, reinterpret_cast<const SparseWork*>(d + P.o_spw), P.n_sparse, sps,
+                                    s->stream);
+    });
   const double entries = (double)(1ull << (2 * s->n));
   const bool herm = s->prec == TQ_FP64 && s->herm_mode && s->herm_ok;
   for (size_t b = 0; b < P.params.size() && e == cudaSuccess; ++b) {
@@ -302,11 +327,16 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
       s->lower_stale = true;
     }
     const void* S = s->prec == TQ_FP64 ? (const void*)(sb64 + P.sb_off[b]) : (const void*)(sb32 + P.sb_off[b]);
-    const int kind = (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
-    e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream); });
+    const bool sparse = p.sparse && s->prec == TQ_FP64 && P.sp_slot[b] >= 0;
+    if (!sparse) p.sparse = 0;
+    const int kind = sparse ? K_SPARSE64 + p.width - 1 : (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
+    const SparseBlock* spb = sparse ? sps + P.sp_slot[b] : nullptr;
+    e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream, spb); });
     if (s->prof_on) {  // per launch: the groups computed x (8 * 16^w flops, 2 * B * 4^w bytes) each
       const double per = (double)(1 << (2 * p.width));
-      s->prof_flops[kind] = 8.0 * groups * per * per;
+      // sparse blocks: the structural nonzeros (exact zeros are skipped, so
+      // the work done can only be smaller)
+      s->prof_flops[kind] = 8.0 * groups * (sparse ? (double)P.nnz[b] : per * per);
       s->prof_bytes[kind] = 2.0 * groups * per * (double)entry_bytes(s->prec);
     }
     (void)entries;
@@ -380,8 +410,12 @@ tq_status run_impl(tq_state* s, const tq_op* ops, size_t n_ops, int width, size_
   P.n_work = plan.n_work;
   P.params.swap(plan.params);
   P.sb_off.swap(plan.sb_off);
+  P.sp_slot.swap(plan.sp_slot);
+  P.nnz.swap(plan.nnz);
+  P.n_sparse = plan.n_sparse;
   P.o_kraus = plan.o_kraus; P.o_ops = plan.o_ops; P.o_blk = plan.o_blk; P.o_mem = plan.o_mem;
-  P.o_work = plan.o_work; P.blob_bytes = plan.blob_bytes;
+  P.o_work = plan.o_work; P.o_spw = plan.o_spw; P.blob_bytes = plan.blob_bytes;
+  if (P.n_sparse > 0 && (st = ensure(s, P.sps, (size_t)P.n_sparse * sizeof(SparseBlock))) != TQ_OK) return st;
   if ((st = ensure(s, P.blob, P.blob_bytes)) != TQ_OK) return st;
   if ((st = ensure(s, P.sops, t.sop_entries * sizeof(double2))) != TQ_OK) return st;
   if ((st = ensure(s, P.sb64, t.sb_entries * sizeof(double2))) != TQ_OK) return st;
@@ -456,7 +490,7 @@ void tq_free(tq_state* s) {
   cudaStreamSynchronize(s->stream);
   if (s->owns_rho && s->rho) cudaFree(s->rho);
   for (DevBuf* b : {&s->red, &s->probs, &s->staging, &s->scratch.blob, &s->scratch.sops, &s->scratch.sb64,
-                    &s->scratch.sb32})
+                    &s->scratch.sb32, &s->scratch.sps})
     free_buf(*b);
   for (PinBuf* b : {&s->pin, &s->pin_small})
     if (b->ptr) cudaFreeHost(b->ptr);
@@ -626,6 +660,7 @@ tq_status tq_program_create(int n, int precision, const tq_op* ops, size_t n_ops
   if (e == cudaSuccess) e = grow(P->sops, t.sop_entries * sizeof(double2) + 16, nullptr, false);
   if (e == cudaSuccess) e = grow(P->sb64, t.sb_entries * sizeof(double2) + 16, nullptr, false);
   if (e == cudaSuccess && precision == TQ_SPLIT) e = grow(P->sb32, t.sb_entries * sizeof(float2) + 16, nullptr, false);
+  if (e == cudaSuccess && P->n_sparse > 0) e = grow(P->sps, (size_t)P->n_sparse * sizeof(SparseBlock), nullptr, false);
   if (e == cudaSuccess) {
     std::vector<char> h(P->blob_bytes);
     pack_blob(*P, t, h.data());
@@ -662,7 +697,7 @@ tq_status tq_program_info(const tq_program* p, size_t* n_ops, size_t* n_blocks, 
 
 void tq_program_free(tq_program* p) {
   if (!p) return;
-  for (DevBuf* b : {&p->blob, &p->sops, &p->sb64, &p->sb32}) free_buf(*b);
+  for (DevBuf* b : {&p->blob, &p->sops, &p->sb64, &p->sb32, &p->sps}) free_buf(*b);
   delete p;
 }
 

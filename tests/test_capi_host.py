@@ -210,3 +210,46 @@ def test_fusion_respects_commutation_barriers(lib):
     assert boo[0] != boo[2] and boo[0] < boo[1] < boo[2]
     boo, widths = B.plan_fusion(2, ops, 2)
     assert boo == [0, 0, 0]
+
+
+def _superop(Ks):
+    # S = sum conj(K) (x) K with local index r + d c: numpy.kron(conj(K), K)
+    return sum(np.kron(np.conj(K), K) for K in Ks)
+
+
+@pytest.mark.parametrize("op", [
+    ("rzz", [0, 1], (0.3,)), ("cx", [0, 1], ()), ("cz", [1, 0], ()), ("rz", [0], (1.1,)), ("h", [0], ()),
+    ("rx", [0], (0.4,)), ("su2", [0], (0.1, 0.2, 0.3, 0.4)),
+    ("depol", [0], (0.01,)), ("depol", [0, 1], (0.05,)), ("ad", [0], (0.2,)), ("pd", [0], (0.3,)),
+    ("thermal", [0], (5e-8, 1e-4, 8e-5)),
+])
+def test_op_patterns_cover_the_superoperator(lib, op):
+    name, q, params = op
+    pat = B.op_pattern(op)
+    if name in O.ONE_QUBIT_GATES or name in O.TWO_QUBIT_GATES:
+        Ks = [O.gate_matrix(name, params)]
+    elif name == "depol":
+        Ks = B.channel_kraus("depol", len(q), params)
+    elif name == "thermal":
+        Ks = B.channel_kraus("thermal", 1, params)
+    else:
+        Ks = O.kraus_matrices(name, params)
+    S = _superop(Ks)
+    nz = np.abs(S) > 1e-15
+    assert pat.shape == S.shape
+    assert np.all(pat[nz])                       # every nonzero is in the pattern
+    if name in ("rzz", "cx", "cz", "rz", "depol", "ad"):
+        assert np.array_equal(pat, nz)           # and the pattern is exact here
+
+
+def test_sparsity_aware_planning():
+    # FP64 is DFMA-bound, so the automatic planner prices a block by its
+    # nonzeros: the TFIM step stays in blocks of at most 2 qubits
+    c = W.tfim_ring(6, 1)
+    _, w64 = B.plan_fusion(6, c.ops, -1, "fp64")
+    _, w32 = B.plan_fusion(6, c.ops, -1, "split")
+    assert max(w64) <= 2 and w32 == [2] * 6
+    assert B.op_pattern(("rzz", [0, 1], (0.2,))).sum() == 16        # diagonal
+    assert B.op_pattern(("depol", [0, 1], (0.1,))).sum() == 28      # 12 coherences + 4 x 4 populations
+    assert B.op_pattern(("depol", [0], (0.1,))).sum() == 6
+    assert B.op_pattern(("cx", [0, 1], ())).sum() == 16             # a permutation
