@@ -223,6 +223,103 @@ cudaError_t run_sparse(double2* rho, const SparseBlock* sp, const ApplyParams& p
   return cudaGetLastError();
 }
 
+// Hermitian mode for split states (widths 1, 2). The pass is HBM-bound, so
+// the canonical groups are walked in T x T tiles: row-rest a in
+// [ta T, ta T + T), column-rest b in [tb T, tb T + T), ta <= tb, one thread
+// per group with consecutive threads along a. Entries on or above the
+// diagonal are read and written in place (coalesced along a); entries below
+// it are held by their transposes, whose rows follow a, so a warp touches 16
+// rows there, and the neighbouring warps of the same tile use the rest of
+// each 32-byte sector while it is still in L1. Diagonal tiles (ta == tb)
+// compute the groups with a <= b.
+//
+// Row index r = dep(a) + rt[l], column index c = dep(b) + ct[l], vec index
+// r + c 2^n; dep() inserts zeros at the target qubits (the same positions for
+// rows and columns) and is additive over disjoint bits, so dep(a0 + i) =
+// dep(a0) + dep(i) for a tile base a0 (a multiple of T): the index math is
+// table lookups and adds.
+template <int K, int T>
+__global__ void __launch_bounds__(T * T) k_apply_herm_tiled(float2* rho, const float2* __restrict__ S,
+                                                            const __grid_constant__ ApplyParams p) {
+  constexpr int D = 1 << (2 * K);
+  __shared__ float2 sS[D * D];
+  __shared__ unsigned int s_dep[T];          // deposit of i < T into the non-target positions
+  __shared__ unsigned int s_rt[D], s_ct[D];  // row / column target bits of local index l
+  int qs[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) qs[j] = p.q[j];
+#pragma unroll
+  for (int x = 0; x < K; ++x)  // sort the target qubits ascending
+#pragma unroll
+    for (int y = 0; y + 1 < K; ++y)
+      if (qs[y] > qs[y + 1]) {
+        const int t = qs[y];
+        qs[y] = qs[y + 1];
+        qs[y + 1] = t;
+      }
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sS[i] = S[i];
+  if (threadIdx.x < T) s_dep[threadIdx.x] = (unsigned int)deposit_zeros(threadIdx.x, qs, K);
+  if (threadIdx.x < D) {
+    unsigned int rt = 0, ct = 0;
+    for (int j = 0; j < K; ++j) {
+      rt |= ((threadIdx.x >> j) & 1u) << p.q[j];
+      ct |= ((threadIdx.x >> (K + j)) & 1u) << p.q[j];
+    }
+    s_rt[threadIdx.x] = rt;
+    s_ct[threadIdx.x] = ct;
+  }
+  __syncthreads();
+  const unsigned int* rt = s_rt;  // warp-uniform reads (broadcast)
+  const unsigned int* ct = s_ct;
+  const int i = threadIdx.x % T, j = threadIdx.x / T;
+  const unsigned int di = s_dep[i], dj = s_dep[j];
+  const unsigned long long Mt = (1ull << (p.n - K)) / T;
+  const unsigned long long n_tiles = Mt * (Mt + 1) / 2;
+  for (unsigned long long u = blockIdx.x; u < n_tiles; u += gridDim.x) {
+    bool diag = false;
+    const unsigned long long tt = canonical_group(u, 32, &diag);  // (ta, tb) as ta | tb << 32
+    if (diag && i > j) continue;  // not a canonical group
+    const bool self = diag && i == j;
+    const unsigned int rbase = (unsigned int)deposit_zeros((tt & 0xffffffffull) * T, qs, K) + di;
+    const unsigned int cbase = (unsigned int)deposit_zeros((tt >> 32) * T, qs, K) + dj;
+    float2 x[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      const unsigned int r = rbase + rt[l], c = cbase + ct[l];
+      const bool up = r <= c;
+      float2 v = rho[up ? ((unsigned long long)r | ((unsigned long long)c << p.n))
+                        : ((unsigned long long)c | ((unsigned long long)r << p.n))];
+      if (!up) v.y = -v.y;
+      x[l] = v;
+    }
+#pragma unroll
+    for (int o = 0; o < D; ++o) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+        CplxOps<float2>::fma(acc, K == 1 ? sS[o * D + l] : CplxOps<float2>::lds(&sS[o * D + l]), x[l]);
+      const unsigned int r = rbase + rt[o], c = cbase + ct[o];
+      if (r <= c) {
+        rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+      } else if (!self) {  // a self-conjugate group writes its upper entries only
+        acc.y = -acc.y;
+        rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+      }
+    }
+  }
+}
+
+template <int K>
+cudaError_t run_herm_tiled_split(float2* rho, const float2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
+  constexpr int T = 16;
+  const unsigned long long M = 1ull << (p.n - K);
+  if (M < T) return cudaErrorInvalidValue;  // the caller uses full updates for tiny registers
+  const unsigned long long Mt = M / T, n_tiles = Mt * (Mt + 1) / 2;
+  const int grid = (int)std::max<unsigned long long>(1, std::min<unsigned long long>(n_tiles, (unsigned long long)num_sms * 8));
+  k_apply_herm_tiled<K, T><<<grid, T * T, 0, st>>>(rho, S, p);
+  return cudaGetLastError();
+}
+
 // Widths 3 and 4: a CTA stages the entries of G consecutive groups (4^K x G)
 // in shared memory, then thread (rowset, gi) computes rows i = rowset +
 // (256/G) r of group gi and writes them straight back to global memory (the
@@ -382,7 +479,11 @@ cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyPar
   } else {
     float2* r = static_cast<float2*>(rho);
     const float2* s = static_cast<const float2*>(S);
-    if (p.herm) return cudaErrorInvalidValue;  // split states always update every group
+    if (p.herm) {
+      if (p.width == 1) return run_herm_tiled_split<1>(r, s, p, num_sms, st);
+      if (p.width == 2) return run_herm_tiled_split<2>(r, s, p, num_sms, st);
+      return cudaErrorInvalidValue;  // split Hermitian mode covers widths 1 and 2
+    }
     switch (p.width) {
       case 1: return run_direct<float2, 1, false>(r, s, p, num_sms, st);
       case 2: return run_direct<float2, 2, false>(r, s, p, num_sms, st);

@@ -125,11 +125,11 @@ cudaError_t launch_diag_probs(const void* rho, int n, int precision, const doubl
                               double* out, cudaStream_t st);
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, size_t count, cudaStream_t st);
 cudaError_t launch_convert_f32_to_f64(const float* in, double* out, size_t count, cudaStream_t st);
-// Hermitian mode helpers (FP64 states): fill every entry with row > column
-// from the conjugate of its transpose; and measure max |rho - rho^dagger| and
-// max |rho| (two doubles at out, as non-negative bit patterns via atomicMax).
-cudaError_t launch_mirror_lower(double2* rho, int n, cudaStream_t st);
-cudaError_t launch_hermiticity(const double2* rho, int n, double* out, cudaStream_t st);
+// Hermitian mode helpers: fill every entry with row > column from the
+// conjugate of its transpose; and measure max |rho - rho^dagger| and max
+// |rho| (two doubles at out, as non-negative bit patterns via atomicMax).
+cudaError_t launch_mirror_lower(void* rho, int n, int precision, cudaStream_t st);
+cudaError_t launch_hermiticity(const void* rho, int n, int precision, double* out, cudaStream_t st);
 
 // --- apply kernels (tq_apply.cu) ------------------------------------------
 // One pass of a fused block over vec(rho). S: 4^K x 4^K superoperator,

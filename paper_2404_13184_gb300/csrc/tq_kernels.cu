@@ -236,32 +236,35 @@ __global__ void k_diag_probs(const T2* __restrict__ rho, int n, const double* __
     out[x] = (double)rho[x * (N + 1)].x * scale;
 }
 
-__global__ void k_mirror_lower(double2* rho, int n) {
+template <typename T2>
+__global__ void k_mirror_lower(T2* rho, int n) {
   const unsigned long long N = 1ull << n, total = N * N;
   for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < total;
        e += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long r = e & (N - 1), c = e >> n;
     if (r > c) {
-      const double2 v = rho[c | (r << n)];
-      rho[e] = make_double2(v.x, -v.y);
+      T2 v = rho[c | (r << n)];
+      v.y = -v.y;
+      rho[e] = v;
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_hermiticity(const double2* __restrict__ rho, int n, double* out) {
+template <typename T2>
+__global__ void __launch_bounds__(256) k_hermiticity(const T2* __restrict__ rho, int n, double* out) {
   __shared__ double s_d[256], s_m[256];
   const unsigned long long N = 1ull << n, total = N * N;
   double d = 0.0, m = 0.0;
   for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < total;
        e += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long r = e & (N - 1), c = e >> n;
-    const double2 v = rho[e];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const T2 v = rho[e];
+    m = fmax(m, fmax(fabs((double)v.x), fabs((double)v.y)));
     if (r < c) {
-      const double2 w = rho[c | (r << n)];
-      d = fmax(d, fmax(fabs(v.x - w.x), fabs(v.y + w.y)));
+      const T2 w = rho[c | (r << n)];
+      d = fmax(d, fmax(fabs((double)v.x - (double)w.x), fabs((double)v.y + (double)w.y)));
     } else if (r == c) {
-      d = fmax(d, fabs(v.y));
+      d = fmax(d, fabs((double)v.y));
     }
   }
   s_d[threadIdx.x] = d;
@@ -355,19 +358,25 @@ cudaError_t launch_diag_probs(const void* rho, int n, int precision, const doubl
   return cudaGetLastError();
 }
 
-cudaError_t launch_mirror_lower(double2* rho, int n, cudaStream_t st) {
+cudaError_t launch_mirror_lower(void* rho, int n, int precision, cudaStream_t st) {
   const unsigned long long total = 1ull << (2 * n);
   const int grid = (int)std::min<unsigned long long>(152 * 16, (total + 255) / 256);
-  k_mirror_lower<<<grid, 256, 0, st>>>(rho, n);
+  if (precision == 0)
+    k_mirror_lower<double2><<<grid, 256, 0, st>>>(static_cast<double2*>(rho), n);
+  else
+    k_mirror_lower<float2><<<grid, 256, 0, st>>>(static_cast<float2*>(rho), n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_hermiticity(const double2* rho, int n, double* out, cudaStream_t st) {
+cudaError_t launch_hermiticity(const void* rho, int n, int precision, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const unsigned long long total = 1ull << (2 * n);
   const int grid = (int)std::min<unsigned long long>(152 * 8, (total + 255) / 256);
-  k_hermiticity<<<grid, 256, 0, st>>>(rho, n, out);
+  if (precision == 0)
+    k_hermiticity<double2><<<grid, 256, 0, st>>>(static_cast<const double2*>(rho), n, out);
+  else
+    k_hermiticity<float2><<<grid, 256, 0, st>>>(static_cast<const float2*>(rho), n, out);
   return cudaGetLastError();
 }
 

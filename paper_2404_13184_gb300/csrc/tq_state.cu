@@ -315,16 +315,24 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
                                     s->stream);
     });
   const double entries = (double)(1ull << (2 * s->n));
-  const bool herm = s->prec == TQ_FP64 && s->herm_mode && s->herm_ok;
+  const bool herm_state = s->herm_mode && s->herm_ok;
   for (size_t b = 0; b < P.params.size() && e == cudaSuccess; ++b) {
     ApplyParams p = P.params[b];
     double groups = (double)p.n_groups;
+    // FP64 kernels all have a Hermitian path; split ones for widths 1-2 on
+    // registers with at least 16 row-rest values (tiles of 16 x 16 groups)
+    const bool herm = herm_state && (s->prec == TQ_FP64 || (p.width <= 2 && s->n - p.width >= 4));
     if (herm) {
       const unsigned long long M = 1ull << (s->n - p.width);
       p.herm = 1;
       p.n_canon = M * (M + 1) / 2;
       groups = (double)p.n_canon;
       s->lower_stale = true;
+    } else if (s->lower_stale) {  // a full update needs every entry current
+      s->launches += 1;
+      e = launch_mirror_lower(s->rho, s->n, s->prec, s->stream);
+      s->lower_stale = false;
+      if (e != cudaSuccess) break;
     }
     const void* S = s->prec == TQ_FP64 ? (const void*)(sb64 + P.sb_off[b]) : (const void*)(sb32 + P.sb_off[b]);
     const bool sparse = p.sparse && s->prec == TQ_FP64 && P.sp_slot[b] >= 0;
@@ -471,6 +479,25 @@ tq_status reduce_impl(tq_state* s, const unsigned long long* masks, int n_masks,
   return TQ_OK;
 }
 
+// After tq_set_rho: Hermitian mode stays on only if the new rho is Hermitian
+// to rounding (max |rho - rho^dagger| <= 4 eps max |rho|, checked on the GPU).
+tq_status check_hermitian(tq_state* s) {
+  tq_status st = ensure(s, s->red, kRedBytes);
+  if (st != TQ_OK) return st;
+  if ((st = ensure_pinned(s, s->pin_small, 4096)) != TQ_OK) return st;
+  double* dres = reinterpret_cast<double*>(static_cast<char*>(s->red.ptr) + kRedOut);
+  double* hres = static_cast<double*>(s->pin_small.ptr) + 64;
+  cudaError_t e = launch_hermiticity(s->rho, s->n, s->prec, dres, s->stream);
+  s->launches += 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hres, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  const double eps = s->prec == TQ_FP64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+  s->herm_ok = hres[0] <= 4.0 * eps * hres[1];
+  s->lower_stale = false;
+  return TQ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -523,7 +550,7 @@ tq_status tq_rho_device_ptr(tq_state* s, void** out) {
   if (!s || !out) return TQ_ERR_ARG;
   if (s->lower_stale && !s->poisoned) {
     s->launches += 1;
-    tq_status st = cuda_fail(s, launch_mirror_lower(static_cast<double2*>(s->rho), s->n, s->stream));
+    tq_status st = cuda_fail(s, launch_mirror_lower(s->rho, s->n, s->prec, s->stream));
     if (st != TQ_OK) return st;
     s->lower_stale = false;
   }
@@ -536,7 +563,7 @@ tq_status tq_set_hermitian(tq_state* s, int on) {
   if (st != TQ_OK) return st;
   if (!on && s->lower_stale) {
     s->launches += 1;
-    st = cuda_fail(s, launch_mirror_lower(static_cast<double2*>(s->rho), s->n, s->stream));
+    st = cuda_fail(s, launch_mirror_lower(s->rho, s->n, s->prec, s->stream));
     if (st != TQ_OK) return st;
     s->lower_stale = false;
   }
@@ -546,7 +573,7 @@ tq_status tq_set_hermitian(tq_state* s, int on) {
 
 tq_status tq_is_hermitian_mode(const tq_state* s, int* active) {
   if (!s || !active) return TQ_ERR_ARG;
-  *active = (s->prec == TQ_FP64 && s->herm_mode && s->herm_ok) ? 1 : 0;
+  *active = (s->herm_mode && s->herm_ok) ? 1 : 0;
   return TQ_OK;
 }
 
@@ -565,6 +592,8 @@ tq_status tq_get_rho(tq_state* s, double* out) {
   }
   const size_t chunk = std::min<size_t>(entries, 1ull << 22);  // complex entries per pass
   if ((st = ensure(s, s->staging, chunk * 16)) != TQ_OK) return st;
+  void* full = nullptr;
+  if ((st = tq_rho_device_ptr(s, &full)) != TQ_OK) return st;  // fills the lower triangle if needed
   for (size_t c0 = 0; c0 < entries; c0 += chunk) {
     const size_t cnt = std::min(chunk, entries - c0);
     e = launch_convert_f32_to_f64(static_cast<const float*>(s->rho) + 2 * c0, static_cast<double*>(s->staging.ptr),
@@ -587,19 +616,7 @@ tq_status tq_set_rho(tq_state* s, const double* in) {
   if (s->prec == TQ_FP64) {
     e = cudaMemcpyAsync(s->rho, in, entries * 16, cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e);
-    // Hermitian mode stays on only if the new rho is Hermitian to rounding
-    if ((st = ensure(s, s->red, kRedBytes)) != TQ_OK) return st;
-    if ((st = ensure_pinned(s, s->pin_small, 4096)) != TQ_OK) return st;
-    double* dres = reinterpret_cast<double*>(static_cast<char*>(s->red.ptr) + kRedOut);
-    double* hres = static_cast<double*>(s->pin_small.ptr) + 64;
-    e = launch_hermiticity(static_cast<const double2*>(s->rho), s->n, dres, s->stream);
-    s->launches += 1;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hres, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e);
-    s->herm_ok = hres[0] <= 4.0 * 2.220446049250313e-16 * hres[1];
-    s->lower_stale = false;
-    return TQ_OK;
+    return check_hermitian(s);
   }
   const size_t chunk = std::min<size_t>(entries, 1ull << 22);
   if ((st = ensure(s, s->staging, chunk * 16)) != TQ_OK) return st;
@@ -613,7 +630,7 @@ tq_status tq_set_rho(tq_state* s, const double* in) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e);
   }
-  return TQ_OK;
+  return check_hermitian(s);
 }
 
 tq_status tq_apply_gate(tq_state* s, const int* qubits, int k, const double* U) {

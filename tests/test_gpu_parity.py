@@ -373,3 +373,23 @@ def test_hermitian_mode_follows_set_rho(tq):
         st.reset()
         st.set_hermitian(True)
         assert st.hermitian_mode()
+
+
+@pytest.mark.parametrize("width", [0, 1, 2, 3, -1])
+@pytest.mark.parametrize("n", [5, 6, 9])
+def test_split_hermitian_mode_matches_oracle(tq, n, width):
+    # split Hermitian mode runs widths 1-2 through coalesced 16 x 16 group
+    # tiles (direct or transposed per local index); width-3 blocks in the mix
+    # fill the lower triangle first and update every group
+    c = W.random_noisy_circuit(n, 70, 90 + n + width, gate_set=("h", "s", "rx", "cx", "su2", "rzz"))
+    want = O.run_circuit(n, c.ops)
+    with tq.State(n, "split") as a, tq.State(n, "split", hermitian=False) as b:
+        assert a.hermitian_mode()
+        a.run(c.ops, width=width)
+        b.run(c.ops, width=width)
+        ra, rb = a.rho(), b.rho()
+        masks = [1, 3, (1 << n) - 1]
+        za = a.expect_z(masks)
+    assert maxabs(ra, want) < 2e-6
+    assert maxabs(ra, rb) < 2e-6
+    assert maxabs(za, [O.expect_z(want, m) for m in masks]) < 1e-5
