@@ -36,7 +36,19 @@ library only through its documented API, never through code):
   rho00 -> rho00 + (1-e^{-t/T1}) rho11, rho11 -> e^{-t/T1} rho11 and
   rho01 -> e^{-t/T2} rho01 (rho10 likewise);
 * phase damping with lambda keeps populations and scales coherences by
-  sqrt(1-lambda).
+  sqrt(1-lambda);
+* reset of a qubit to |0> has Kraus operators |0><0| and |0><1|;
+* measuring qubit q with outcome m projects with P_m = |m><m| on q and
+  renormalises: rho -> P_m rho P_m / Tr(P_m rho); the outcome is 0 when a
+  uniform draw u is below Tr(P_0 rho) / Tr(rho);
+* readout error (Sec. 3.5): qubit q reads 1 when prepared in 0 with
+  probability e10[q] and 0 when prepared in 1 with e01[q], independently per
+  qubit, applied to the outcome probabilities of measuring every qubit;
+* sampling a shot from outcome probabilities p takes the smallest x with
+  u < sum_{y <= x} p[y] / sum p (inverse cumulative distribution).
+
+The measurement and reset section announced in the paper is missing from
+its text; these are the textbook definitions.
 
 An op is a tuple ``(name, qubits, params)`` as produced by the workload
 generators; ``("kraus", qubits, [K0, K1, ...])`` and ``("unitary", qubits,
@@ -56,6 +68,7 @@ __all__ = [
     "gate_matrix", "kraus_matrices", "apply_kraus", "apply_kraus_kron",
     "apply_depolarizing", "apply_thermal", "apply_op", "zero_state",
     "run_circuit", "trace", "expect_z", "probabilities", "sv_run",
+    "measure", "readout_probabilities", "sample",
     "ONE_QUBIT_GATES", "TWO_QUBIT_GATES",
 ]
 
@@ -148,6 +161,10 @@ def kraus_matrices(name: str, params=()) -> list[np.ndarray]:
         lam = float(params[0])
         k0 = np.array([[1, 0], [0, math.sqrt(1 - lam)]], dtype=np.complex128)
         k1 = np.array([[0, 0], [0, math.sqrt(lam)]], dtype=np.complex128)
+        return [k0, k1]
+    if name == "reset":
+        k0 = np.array([[1, 0], [0, 0]], dtype=np.complex128)
+        k1 = np.array([[0, 1], [0, 0]], dtype=np.complex128)
         return [k0, k1]
     raise ValueError(f"no Kraus set for {name!r}")
 
@@ -267,7 +284,7 @@ def apply_op(rho: np.ndarray, op) -> np.ndarray:
         return apply_kraus(rho, [np.asarray(K) for K in params], qubits)
     if name == "depol":
         return apply_depolarizing(rho, float(params[0]), qubits)
-    if name in ("ad", "pd"):
+    if name in ("ad", "pd", "reset"):
         return apply_kraus(rho, kraus_matrices(name, params), qubits)
     if name == "thermal":
         t, t1, t2 = (float(v) for v in params)
@@ -348,3 +365,42 @@ def sv_run(n: int, ops) -> np.ndarray:
             order[a] = k + pos
         psi = np.transpose(res, order)
     return psi.reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# Measurement, readout error and sampling
+# --------------------------------------------------------------------------
+
+def measure(rho: np.ndarray, qubit: int, u: float):
+    """Selective measurement of one qubit: (outcome, probability, new rho)."""
+    n = int(round(math.log2(rho.shape[0])))
+    _check_qubits(n, [qubit])
+    d = np.real(np.diag(rho))
+    x = np.arange(rho.shape[0])
+    p0 = float(np.sum(d[((x >> qubit) & 1) == 0]))
+    tr = float(np.sum(d))
+    m = 0 if u < p0 / tr else 1
+    pm = p0 if m == 0 else tr - p0
+    P = np.zeros((2, 2), dtype=np.complex128)
+    P[m, m] = 1.0
+    out = apply_kraus(rho, [P], [qubit]) / pm
+    return m, pm / tr, out
+
+
+def readout_probabilities(p: np.ndarray, e10, e01) -> np.ndarray:
+    """Outcome probabilities after independent per-qubit readout errors:
+    the 2x2 confusion matrix [[1-e10, e01], [e10, 1-e01]] on every qubit."""
+    p = np.array(p, dtype=np.float64)
+    n = int(round(math.log2(p.shape[0])))
+    t = p.reshape((2,) * n)
+    for q in range(n):
+        A = np.array([[1 - e10[q], e01[q]], [e10[q], 1 - e01[q]]])
+        ax = n - 1 - q
+        t = np.moveaxis(np.tensordot(A, t, axes=([1], [ax])), 0, ax)
+    return t.reshape(-1)
+
+
+def sample(p: np.ndarray, uniforms) -> np.ndarray:
+    """Inverse-CDF samples: for each u the smallest x with u < cdf[x] / cdf[-1]."""
+    cdf = np.cumsum(np.asarray(p, dtype=np.float64))
+    return np.searchsorted(cdf / cdf[-1], np.asarray(uniforms), side="right")

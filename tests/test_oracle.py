@@ -335,3 +335,46 @@ def test_workload_shapes():
     assert c3.n == 15 and c3.n_gates == 900 and len(c3.steps) == 30
     assert sum(1 for o in c3.ops if o[0] in ("rzz", "rx")) == 900
     assert W.plain_6q().ops == c1.ops          # seeded: identical on regeneration
+
+
+# ------------------------------------------------ measurement, reset, readout
+
+def test_reset_closed_forms():
+    assert np.allclose(O.apply_op(ket(1, 1), ("reset", [0], ())), ket(1, 0))
+    rho = W.random_density_matrix(3, 8)
+    out = O.apply_op(rho, ("reset", [1], ()))
+    # qubit 1 ends in |0>, the reduced state of qubits 0 and 2 is unchanged
+    t_in = rho.reshape(2, 2, 2, 2, 2, 2)      # (q2, q1, q0) x (q2, q1, q0)
+    t_out = out.reshape(2, 2, 2, 2, 2, 2)
+    assert np.allclose(np.einsum("aibcid->abcd", t_in), np.einsum("aibcid->abcd", t_out), atol=1e-15)
+    assert np.allclose(t_out[:, 1], 0) and np.allclose(t_out[:, :, :, :, 1], 0)
+    assert abs(O.trace(out) - 1) < 1e-14
+
+
+def test_measurement_closed_forms():
+    n = 3
+    ghz = O.run_circuit(n, W.ghz(n))
+    m, p, post = O.measure(ghz, 1, 0.25)
+    assert m == 0 and abs(p - 0.5) < 1e-15 and np.allclose(post, ket(n, 0))
+    m, p, post = O.measure(ghz, 2, 0.75)
+    assert m == 1 and abs(p - 0.5) < 1e-15 and np.allclose(post, ket(n, 7))
+    # |+> on qubit 0: measuring gives each outcome with probability 1/2; a mixed state keeps its rest
+    rho = O.run_circuit(2, [("h", [0], ()), ("ad", [1], (0.3,)), ("h", [1], ())])
+    m, p, post = O.measure(rho, 0, 0.9)
+    assert m == 1 and abs(p - 0.5) < 1e-15
+    assert abs(O.trace(post) - 1) < 1e-15 and abs(O.expect_z(post, 1) + 1) < 1e-15
+
+
+def test_readout_and_sampling():
+    # one qubit: the confusion matrix itself
+    out = O.readout_probabilities([0.8, 0.2], [0.1], [0.3])
+    assert np.allclose(out, [0.8 * 0.9 + 0.2 * 0.3, 0.8 * 0.1 + 0.2 * 0.7])
+    # independent qubits: a product distribution stays a product of confused factors
+    pa, pb = np.array([0.6, 0.4]), np.array([0.25, 0.75])
+    p = np.kron(pb, pa)                               # qubit 0 = low bit
+    e10, e01 = [0.02, 0.05], [0.1, 0.07]
+    want = np.kron(O.readout_probabilities(pb, [e10[1]], [e01[1]]), O.readout_probabilities(pa, [e10[0]], [e01[0]]))
+    assert np.allclose(O.readout_probabilities(p, e10, e01), want, atol=1e-15)
+    assert abs(np.sum(O.readout_probabilities(np.full(8, 1 / 8), [0.1] * 3, [0.2] * 3)) - 1) < 1e-15
+    assert list(O.sample([0.5, 0.0, 0.25, 0.25], [0.1, 0.49, 0.5, 0.74, 0.76, 0.999])) == [0, 0, 2, 2, 3, 3]
+    assert list(O.sample(np.eye(4)[2], [0.0, 0.5, 0.9999])) == [2, 2, 2]
