@@ -96,12 +96,16 @@ typedef enum {
  *  THERMAL       params = (t, T1, T2), t >= 0, T1 > 0, 0 < T2 <= 2 T1:
  *                zero-temperature relaxation rho00 += (1-e^{-t/T1}) rho11,
  *                rho11 *= e^{-t/T1}, rho01 *= e^{-t/T2}; applied
- *                independently to each of the k (1..2) listed qubits. */
+ *                independently to each of the k (1..2) listed qubits.
+ *  RESET         no parameters: the qubit is reset to |0>, K0 = |0><0|,
+ *                K1 = |0><1|; k = 1 (the reset gate announced in Sec. 3,
+ *                whose section the paper does not contain). */
 typedef enum {
   TQ_CH_DEPOLARIZING = 0,
   TQ_CH_AMPLITUDE_DAMPING = 1,
   TQ_CH_PHASE_DAMPING = 2,
-  TQ_CH_THERMAL = 3
+  TQ_CH_THERMAL = 3,
+  TQ_CH_RESET = 4
 } tq_channel;
 
 typedef enum {
@@ -392,6 +396,33 @@ tq_status tq_profile_read(tq_state* s, tq_kernel_stat* out, int capacity, int* c
 
 /* Total kernels this state has launched since creation (always counted). */
 tq_status tq_launch_count(const tq_state* s, uint64_t* out);
+
+/* ---- measurement (Sec. 3 announces measurement gates; Sec. 3.5 the
+ * readout-error model; the measurement section itself is missing) -------- */
+
+/* Selective measurement of `qubit` in the computational basis: with
+ * p0 = Tr(P0 rho)/Tr(rho) (P_m = |m><m| on the qubit, FP64 reduction), the
+ * outcome is 0 if u < p0, else 1 (u in [0,1) is the caller's uniform draw);
+ * rho becomes P_m rho P_m / Tr(P_m rho). *outcome receives m, *probability
+ * (may be NULL) its probability. Waits for the stream. */
+tq_status tq_measure(tq_state* s, int qubit, double u, int* outcome, double* probability);
+
+/* Outcome probabilities of measuring every qubit after independent
+ * per-qubit readout errors: qubit q reads 1 when it is 0 with probability
+ * e10[q] (prob_meas1_prep0) and reads 0 when it is 1 with e01[q]
+ * (prob_meas0_prep1): the confusion matrix [[1-e10, e01], [e10, 1-e01]] on
+ * every qubit, applied on the GPU to diag(rho) (renormalised in TQ_SPLIT).
+ * e10, e01: n rates in [0,1]; out: 2^n doubles. Waits for the stream. */
+tq_status tq_probs_readout(tq_state* s, const double* e10, const double* e01, double* out);
+
+/* Sample `shots` outcomes of measuring every qubit: outcomes[i] = the
+ * smallest x with u[i] < cdf[x] / cdf[2^n - 1], where cdf is the inclusive
+ * prefix sum (FP64, fixed order) of the outcome probabilities, with the
+ * readout errors e10/e01 applied first when both are given (both NULL:
+ * none). u[i] in [0,1) are the caller's uniform draws. Waits for the
+ * stream. */
+tq_status tq_sample(tq_state* s, const double* u, int shots, const double* e10, const double* e01,
+                    uint64_t* outcomes);
 
 /* ---- host-side helpers (no GPU work; usable without a device) ----------- */
 

@@ -26,7 +26,7 @@ STATUS = {0: "TQ_OK", 1: "TQ_ERR_ARG", 2: "TQ_ERR_QUBIT", 3: "TQ_ERR_OOM", 4: "T
           5: "TQ_ERR_TIMEOUT", 6: "TQ_ERR_STATE", 7: "TQ_ERR_UNSUPPORTED"}
 GATES = {"id": 0, "h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "sx": 9,
          "rx": 10, "ry": 11, "rz": 12, "su2": 13, "cx": 32, "cz": 33, "swap": 34, "rzz": 35}
-CHANNELS = {"depol": 0, "ad": 1, "pd": 2, "thermal": 3}
+CHANNELS = {"depol": 0, "ad": 1, "pd": 2, "thermal": 3, "reset": 4}
 OP_UNITARY, OP_KRAUS, OP_GATE, OP_CHANNEL = 0, 1, 2, 3
 
 
@@ -66,6 +66,10 @@ _SIGNATURES = [
     ("tq_trace", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     ("tq_expect_z", c_int, [c_void_p, POINTER(c_uint64), c_int, POINTER(c_double)]),
     ("tq_probs", c_int, [c_void_p, POINTER(c_double)]),
+    ("tq_measure", c_int, [c_void_p, c_int, c_double, POINTER(c_int), POINTER(c_double)]),
+    ("tq_probs_readout", c_int, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    ("tq_sample", c_int, [c_void_p, POINTER(c_double), c_int, POINTER(c_double), POINTER(c_double),
+                          POINTER(c_uint64)]),
     ("tq_program_create", c_int, [c_int, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_void_p)]),
     ("tq_program_run", c_int, [c_void_p, c_void_p]),
     ("tq_program_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int), POINTER(c_size_t)]),
@@ -503,6 +507,28 @@ class State:
     def probs(self) -> np.ndarray:
         out = np.zeros(1 << self.n)
         _check(_lib.tq_probs(self._h, _dptr(out)), "tq_probs")
+        return out
+
+    def measure(self, qubit: int, u: float):
+        """(outcome, probability) of a selective measurement; rho collapses."""
+        m, p = c_int(0), c_double(0)
+        _check(_lib.tq_measure(self._h, qubit, float(u), ctypes.byref(m), ctypes.byref(p)), "tq_measure")
+        return m.value, p.value
+
+    def probs_readout(self, e10, e01) -> np.ndarray:
+        a = np.ascontiguousarray(e10, dtype=np.float64)
+        b = np.ascontiguousarray(e01, dtype=np.float64)
+        out = np.zeros(1 << self.n)
+        _check(_lib.tq_probs_readout(self._h, _dptr(a), _dptr(b), _dptr(out)), "tq_probs_readout")
+        return out
+
+    def sample(self, uniforms, e10=None, e01=None) -> np.ndarray:
+        u = np.ascontiguousarray(uniforms, dtype=np.float64)
+        out = np.zeros(len(u), dtype=np.uint64)
+        a = None if e10 is None else np.ascontiguousarray(e10, dtype=np.float64)
+        b = None if e01 is None else np.ascontiguousarray(e01, dtype=np.float64)
+        _check(_lib.tq_sample(self._h, _dptr(u), len(u), None if a is None else _dptr(a),
+                              None if b is None else _dptr(b), out.ctypes.data_as(POINTER(c_uint64))), "tq_sample")
         return out
 
     def vec(self) -> np.ndarray:

@@ -131,6 +131,13 @@ cudaError_t launch_convert_f32_to_f64(const float* in, double* out, size_t count
 cudaError_t launch_mirror_lower(void* rho, int n, int precision, cudaStream_t st);
 cudaError_t launch_hermiticity(const void* rho, int n, int precision, double* out, cudaStream_t st);
 
+// --- measurement (tq_measure.cu) -------------------------------------------
+// Per-qubit readout confusion on 2^n outcome probabilities (host arrays of
+// n rates); fixed-order CDF and inverse-CDF sampling of `shots` uniforms.
+cudaError_t launch_readout(double* p, int n, const double* e10, const double* e01, cudaStream_t st);
+cudaError_t launch_sample(const double* p, int n, double* cdf, const double* u, int shots, unsigned long long* out,
+                          cudaStream_t st);
+
 // --- apply kernels (tq_apply.cu) ------------------------------------------
 // One pass of a fused block over vec(rho). S: 4^K x 4^K superoperator,
 // row-major (double2 for FP64 states, float2 for split states).

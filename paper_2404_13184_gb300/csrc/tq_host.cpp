@@ -410,6 +410,12 @@ tq_status tq_channel_kraus(int channel, int k, const double* params, int capacit
       add(k1);
       break;
     }
+    case TQ_CH_RESET: {
+      if (k != 1) return TQ_ERR_ARG;
+      add(std::vector<cplx>{1.0, 0.0, 0.0, 0.0});  // |0><0|
+      add(std::vector<cplx>{0.0, 1.0, 0.0, 0.0});  // |0><1|
+      break;
+    }
     case TQ_CH_THERMAL: {
       if (k < 1 || k > 2) return TQ_ERR_ARG;
       const double t = params[0], t1 = params[1], t2 = params[2];

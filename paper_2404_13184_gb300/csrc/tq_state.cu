@@ -3,6 +3,7 @@
 // enqueues kernels; every arithmetic step of the simulation runs on the
 // device (superoperator build and fusion in FP64, apply passes, reductions).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -42,7 +43,7 @@ struct tq_state {
   size_t rho_bytes = 0;
   bool owns_rho = false;
   bool poisoned = false;
-  DevBuf red, probs, staging;
+  DevBuf red, probs, staging, shots;
   PinBuf pin, pin_small;
   cudaEvent_t pin_free = nullptr;  // recorded after the last upload from `pin`
   tq_program scratch;              // plan of the last tq_run_circuit call
@@ -516,7 +517,7 @@ void tq_free(tq_state* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
   if (s->owns_rho && s->rho) cudaFree(s->rho);
-  for (DevBuf* b : {&s->red, &s->probs, &s->staging, &s->scratch.blob, &s->scratch.sops, &s->scratch.sb64,
+  for (DevBuf* b : {&s->red, &s->probs, &s->staging, &s->shots, &s->scratch.blob, &s->scratch.sops, &s->scratch.sb64,
                     &s->scratch.sb32, &s->scratch.sps})
     free_buf(*b);
   for (PinBuf* b : {&s->pin, &s->pin_small})
@@ -749,12 +750,16 @@ tq_status tq_expect_z_device(tq_state* s, const uint64_t* masks_dev, int n_masks
   return reduce_device(s, reinterpret_cast<const unsigned long long*>(masks_dev), n_masks, s->prec == TQ_SPLIT, out_dev);
 }
 
-tq_status tq_probs(tq_state* s, double* out) {
-  tq_status st = check_state(s);
-  if (st != TQ_OK) return st;
-  if (!out) return TQ_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// Outcome probabilities (renormalised for split states) into s->probs on
+// the device, then the optional per-qubit readout confusion.
+tq_status probs_device(tq_state* s, const double* e10, const double* e01) {
   const size_t N = 1ull << s->n;
-  if ((st = ensure(s, s->probs, N * sizeof(double))) != TQ_OK) return st;
+  tq_status st = ensure(s, s->probs, 2 * N * sizeof(double));  // probabilities, then the CDF
+  if (st != TQ_OK) return st;
   const double* tr = nullptr;
   if (s->prec == TQ_SPLIT) {
     double tmp[2];
@@ -763,9 +768,104 @@ tq_status tq_probs(tq_state* s, double* out) {
   }
   cudaError_t e = launch_diag_probs(s->rho, s->n, s->prec, tr, static_cast<double*>(s->probs.ptr), s->stream);
   s->launches += 1;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->probs.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && e10 && e01) {
+    e = launch_readout(static_cast<double*>(s->probs.ptr), s->n, e10, e01, s->stream);
+    s->launches += s->n;
+  }
+  return cuda_fail(s, e);
+}
+
+bool rates_ok(const double* e, int n) {
+  for (int q = 0; q < n; ++q)
+    if (!(e[q] >= 0.0 && e[q] <= 1.0)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+tq_status tq_probs(tq_state* s, double* out) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (!out) return TQ_ERR_ARG;
+  if ((st = probs_device(s, nullptr, nullptr)) != TQ_OK) return st;
+  const size_t N = 1ull << s->n;
+  cudaError_t e = cudaMemcpyAsync(out, s->probs.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_fail(s, e);
+}
+
+tq_status tq_probs_readout(tq_state* s, const double* e10, const double* e01, double* out) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (!out || !e10 || !e01 || !rates_ok(e10, s->n) || !rates_ok(e01, s->n)) return TQ_ERR_ARG;
+  if ((st = probs_device(s, e10, e01)) != TQ_OK) return st;
+  const size_t N = 1ull << s->n;
+  cudaError_t e = cudaMemcpyAsync(out, s->probs.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
+
+tq_status tq_sample(tq_state* s, const double* u, int shots, const double* e10, const double* e01,
+                    uint64_t* outcomes) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (shots < 0 || (shots > 0 && (!u || !outcomes)) || (!e10) != (!e01)) return TQ_ERR_ARG;
+  if (e10 && (!rates_ok(e10, s->n) || !rates_ok(e01, s->n))) return TQ_ERR_ARG;
+  for (int i = 0; i < shots; ++i)
+    if (!(u[i] >= 0.0 && u[i] < 1.0)) return TQ_ERR_ARG;
+  if (shots == 0) return TQ_OK;
+  if ((st = probs_device(s, e10, e01)) != TQ_OK) return st;
+  const size_t N = 1ull << s->n;
+  const size_t bytes = (size_t)shots * 16;
+  if ((st = ensure(s, s->shots, bytes)) != TQ_OK) return st;
+  if ((st = ensure_pinned(s, s->pin, bytes)) != TQ_OK) return st;
+  cudaError_t e = cudaEventSynchronize(s->pin_free);  // the staging buffer is shared with uploads
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  std::memcpy(s->pin.ptr, u, (size_t)shots * sizeof(double));
+  double* du = static_cast<double*>(s->shots.ptr);
+  unsigned long long* dout = reinterpret_cast<unsigned long long*>(du + shots);
+  e = cudaMemcpyAsync(du, s->pin.ptr, (size_t)shots * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = launch_sample(static_cast<const double*>(s->probs.ptr), s->n, static_cast<double*>(s->probs.ptr) + N, du,
+                      shots, dout, s->stream);
+  s->launches += 2;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->pin.ptr, dout, (size_t)shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  std::memcpy(outcomes, s->pin.ptr, (size_t)shots * sizeof(uint64_t));
+  return TQ_OK;
+}
+
+tq_status tq_measure(tq_state* s, int qubit, double u, int* outcome, double* probability) {
+  tq_status st = check_state(s);
+  if (st != TQ_OK) return st;
+  if (qubit < 0 || qubit >= s->n) return TQ_ERR_QUBIT;
+  if (!outcome || !(u >= 0.0 && u < 1.0)) return TQ_ERR_ARG;
+  const unsigned long long mask = 1ull << qubit;
+  double red[3];
+  if ((st = reduce_impl(s, &mask, 1, false, red)) != TQ_OK) return st;  // Re tr, Im tr, Re Tr(rho Z_q)
+  const double tr = red[0];
+  const double p0 = 0.5 * (tr + red[2]);
+  if (!(tr > 0.0)) return TQ_ERR_ARG;
+  const int m = u < p0 / tr ? 0 : 1;
+  const double pm = m == 0 ? p0 : tr - p0;
+  if (!(pm > 0.0)) return TQ_ERR_ARG;
+  // project with |m><m| and renormalise: one Kraus matrix |m><m| / sqrt(p_m)
+  double K[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  K[m == 0 ? 0 : 6] = 1.0 / std::sqrt(pm);
+  tq_op op{};
+  op.kind = TQ_OP_KRAUS;
+  op.k = 1;
+  op.qubits[0] = qubit;
+  op.m = 1;
+  op.mats = K;
+  if ((st = run_impl(s, &op, 1, 0, nullptr)) != TQ_OK) return st;
+  *outcome = m;
+  if (probability) *probability = pm / tr;
+  return TQ_OK;
 }
 
 tq_status tq_profile_enable(tq_state* s, int on) {

@@ -72,7 +72,7 @@ def test_binding_enums_match_header():
         assert g["TQ_GATE_" + k.upper()] == v, k
     c = enums["tq_channel"]
     names = {"depol": "TQ_CH_DEPOLARIZING", "ad": "TQ_CH_AMPLITUDE_DAMPING", "pd": "TQ_CH_PHASE_DAMPING",
-             "thermal": "TQ_CH_THERMAL"}
+             "thermal": "TQ_CH_THERMAL", "reset": "TQ_CH_RESET"}
     for k, v in B.CHANNELS.items():
         assert c[names[k]] == v
     assert enums["tq_precision"] == {"TQ_FP64": 0, "TQ_SPLIT": 1}
@@ -99,7 +99,7 @@ def test_gate_library_matches_oracle(lib, name):
     ("depol", 1, (0.013,)), ("depol", 2, (0.2,)), ("depol", 1, (1.0,)),
     ("ad", 1, (5e-4,)), ("ad", 1, (0.4,)), ("pd", 1, (0.3,)),
     ("thermal", 1, (50e-9, 100e-6, 80e-6)), ("thermal", 2, (300e-9, 100e-6, 80e-6)),
-    ("thermal", 1, (2e-5, 10e-6, 20e-6)),
+    ("thermal", 1, (2e-5, 10e-6, 20e-6)), ("reset", 1, ()),
 ])
 def test_channel_kraus_sets_act_like_the_oracle_channels(lib, name, k, params):
     Ks = B.channel_kraus(name, k, params)
