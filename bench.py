@@ -262,14 +262,14 @@ def autotune_cache():
     return os.path.join(ROOT, "paper_2404_13184_gb300", "autotune_cache.txt")
 
 
-def run_sweep(tq, torch, precision, steps, warmup, count=1024, oracle_sample=12):
+def run_sweep(tq, torch, precision, steps, warmup, count=1024, oracle_sample=12, n_min=4, n_max=11):
     """Batched sweep: `count` independent noisy circuits (n ~ U{4..11}, depth
     ~ U{50..500}, {H, RZ, RX, CX}, per-circuit depolarising p) in one
     persistent launch per run (a CUDA graph replay), tile and fusion width per
     qubit count from the autotuner. Returns throughput, per-circuit readouts
     and the oracle error on a sample of the small circuits."""
     from paper_2404_13184_gb300 import workloads
-    circuits = workloads.sweep(count)
+    circuits = workloads.sweep(count, n_min=n_min, n_max=n_max)
     t_tune = time.perf_counter()
     tuned = {n: tq.autotune(precision, n, autotune_cache()) for n in sorted({c.n for c in circuits})}
     t_tune = time.perf_counter() - t_tune
@@ -453,6 +453,8 @@ def main():
     ap.add_argument("--workload", default="tfim15", choices=["tfim15", "sweep", "serve", "layered12"],
                     help="tfim15: the benchmark line; sweep / serve: the batched-sweep and served-stream workloads")
     ap.add_argument("--precision", default="both", choices=["fp64", "split", "both"], help="sweep / serve modes")
+    ap.add_argument("--sweep-count", type=int, default=1024)
+    ap.add_argument("--sweep-qubits", type=str, default="4-11", help="qubit range of the sweep, e.g. 4-11")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-duration", type=float, default=60.0)
     ap.add_argument("--serve-drain", type=float, default=60.0)
@@ -493,9 +495,11 @@ def main():
         precs = ["fp64", "split"] if args.precision == "both" else [args.precision]
         for prec in precs:
             if args.workload == "sweep":
-                r = run_sweep(tq, torch, prec, args.steps, args.warmup)
+                lo, hi = (int(v) for v in args.sweep_qubits.split("-"))
+                r = run_sweep(tq, torch, prec, args.steps, args.warmup, count=args.sweep_count, n_min=lo, n_max=hi)
                 r.pop("results")
-                line = {"metric": "batched sweep circuits/s", "workload": "sweep-1024 (n 4-11, depth 50-500)",
+                line = {"metric": "batched sweep circuits/s",
+                        "workload": f"sweep-{args.sweep_count} (n {lo}-{hi}, depth 50-500)",
                         "dtype": "f64" if prec == "fp64" else "f32", **r}
             else:
                 r = run_serve(tq, prec, args.serve_rate, args.serve_duration, args.serve_drain)

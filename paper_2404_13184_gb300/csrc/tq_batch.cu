@@ -124,7 +124,7 @@ tq_status finalize(tq_batch* b) {
     const int tl = b->tile_log2_for_n[J.n] ? b->tile_log2_for_n[J.n] : default_tile_log2(J.n, b->prec);
     // at least 16 groups' worth of entries per tile, at most 2^16 tiles per block
     hj.tile_log2 = std::min(std::max({tl, 4, 2 * J.n - 16}), 2 * J.n);
-    if ((long long)hj.n_blocks << (2 * J.n - hj.tile_log2) >= (1ll << 31)) return TQ_ERR_UNSUPPORTED;
+    hj.herm = batch_herm(J.n, b->prec) ? 1 : 0;
     hj.n_masks = (int)J.masks.size();
     hj.never_ready = (int)j == b->never_ready_job ? 1 : 0;
     for (size_t m = 0; m < J.masks.size(); ++m) hj.masks[m] = J.masks[m];
@@ -135,6 +135,8 @@ tq_status finalize(tq_batch* b) {
       bb.S = reinterpret_cast<const void*>(J.prog.sb_off[k] + sbb);  // offset; made absolute below
       hblks.push_back(bb);
     }
+    if (set_tiles(hblks.data() + hj.block0, hj.n_blocks, hj.tile_log2, hj.herm != 0) >= (1ll << 31))
+      return TQ_ERR_UNSUPPORTED;
     arena = align_up(arena + ((size_t)(b->prec == TQ_FP64 ? 16 : 8) << (2 * J.n)), 256);
   }
   b->arena_bytes = arena;
@@ -152,7 +154,7 @@ tq_status finalize(tq_batch* b) {
     for (size_t j = 0; j < hjobs.size(); ++j) {
       const BJob& hj = hjobs[j];
       if (hj.resident || r >= hj.n_blocks) continue;
-      const int tiles = 1 << (2 * hj.n - hj.tile_log2);
+      const int tiles = hblks[hj.block0 + r].tiles;
       for (int t = 0; t < tiles; ++t) items.push_back(BItem{(int)j, r, t, 1});
     }
   b->n_items = items.size();
@@ -204,11 +206,11 @@ tq_status finalize(tq_batch* b) {
 
   const size_t smem = b->prec == TQ_FP64 ? apply_smem<double2>() : apply_smem<float2>();
   if (b->prec == TQ_FP64) {
-    e = cudaFuncSetAttribute(k_batch_apply<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<double2>, kThreads, smem);
+    e = cudaFuncSetAttribute(k_batch_apply<double2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<double2, true, true>, kThreads, smem);
   } else {
-    e = cudaFuncSetAttribute(k_batch_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<float2>, kThreads, smem);
+    e = cudaFuncSetAttribute(k_batch_apply<float2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<float2, true, false>, kThreads, smem);
   }
   if (e != cudaSuccess) return to_status(e);
   b->per_sm = std::max(1, b->per_sm);
@@ -240,12 +242,12 @@ tq_status finalize(tq_batch* b) {
   const int grid = (int)std::max<size_t>(1, std::min<size_t>(b->n_items, (size_t)b->num_sms * b->per_sm));
   if (b->n_items > 0) {
     if (b->prec == TQ_FP64)
-      k_batch_apply<double2><<<grid, kThreads, smem, st>>>(
+      k_batch_apply<double2, true, true><<<grid, kThreads, smem, st>>>(
           static_cast<char*>(b->arena.ptr), static_cast<const BJob*>(b->djobs.ptr),
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
     else
-      k_batch_apply<float2><<<grid, kThreads, smem, st>>>(
+      k_batch_apply<float2, true, false><<<grid, kThreads, smem, st>>>(
           static_cast<char*>(b->arena.ptr), static_cast<const BJob*>(b->djobs.ptr),
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
@@ -367,7 +369,12 @@ tq_status tq_batch_get_rho(tq_batch* b, int job, double* out) {
   if (st != TQ_OK) return st;
   const int n = b->jobs[job].n;
   const size_t entries = 1ull << (2 * n);
-  const char* src = static_cast<const char*>(b->arena.ptr) + b->rho_off[job];
+  char* src = static_cast<char*>(b->arena.ptr) + b->rho_off[job];
+  if (batch_herm(n, b->prec)) {  // Hermitian mode kept rows <= columns only: fill the rest
+    cudaError_t em = launch_mirror_lower(src, n, b->prec, b->stream);
+    if (em == cudaSuccess) em = cudaStreamSynchronize(b->stream);
+    if (em != cudaSuccess) return to_status(em);
+  }
   if (b->prec == TQ_FP64) return to_status(cudaMemcpy(out, src, entries * 16, cudaMemcpyDeviceToHost));
   std::vector<float> tmp(2 * entries);
   cudaError_t e = cudaMemcpy(tmp.data(), src, entries * 8, cudaMemcpyDeviceToHost);

@@ -34,13 +34,15 @@ struct BJob {
   int resident;
   int n_masks;
   int never_ready;  // test hook: this job's waits can never be satisfied
-  int pad;
+  int herm;         // Hermitian mode: canonical groups only, rows <= columns kept
   unsigned long long masks[kMaxMasks];
 };
 
 struct BBlk {
   ApplyParams p;
-  const void* S;  // fused superoperator, 4^w x 4^w row-major (double2 or float2)
+  const void* S;    // fused superoperator, 4^w x 4^w row-major (double2 or float2)
+  int tiles;        // tile items of this block (tile jobs)
+  int tile_prefix;  // tiles of the job's earlier blocks: the wait target
 };
 
 struct BItem {
@@ -84,24 +86,61 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // One group of a width-K block: gather its 4^K entries, multiply by S
 // (shared memory), scatter back. GLOBAL: rho in global memory, loaded
 // through L2 only (other CTAs wrote it); else rho is the shared-memory copy.
-template <typename T2, int K, bool GLOBAL>
-__device__ __forceinline__ void apply_group(T2* rho, unsigned long long g, const ApplyParams& p, const T2* sS) {
+// HERM: t indexes the canonical groups (row rest <= column rest); entries
+// below the diagonal are read and written through their conjugate
+// transposes, as in the single-state kernels. FP64 skips exactly-zero
+// superoperator entries: S is the same for every thread, so the branch is
+// uniform, and the result is unchanged (an FMA with a zero product is exact).
+template <typename T2, int K, bool GLOBAL, bool HERM>
+__device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const ApplyParams& p, const T2* sS) {
   constexpr int D = 1 << (2 * K);
-  unsigned long long base = g;
+  bool self = false;
+  unsigned long long base = HERM ? canonical_group(t, p.n - K, &self) : t;
 #pragma unroll
   for (int i = 0; i < 2 * K; ++i) {
     const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
     base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
   }
+  // Hermitian mode works on 32-bit row / column indices (n <= 16):
+  // r = rows of base + row part of off[l], c likewise.
+  const unsigned int rmask = (1u << p.n) - 1u;
+  const unsigned int rb = (unsigned int)(base & rmask), cb = (unsigned int)(base >> p.n);
   T2 x[D];
 #pragma unroll
-  for (int l = 0; l < D; ++l) x[l] = GLOBAL ? Cx<T2>::ldcg(&rho[base + p.off[l]]) : rho[base + p.off[l]];
+  for (int l = 0; l < D; ++l) {
+    unsigned long long e;
+    bool conj = false;
+    if (HERM) {
+      const unsigned int r = rb + (unsigned int)(p.off[l] & rmask), c = cb + (unsigned int)(p.off[l] >> p.n);
+      conj = r > c;
+      e = conj ? ((unsigned long long)c | ((unsigned long long)r << p.n)) : ((unsigned long long)r | ((unsigned long long)c << p.n));
+    } else {
+      e = base + p.off[l];
+    }
+    T2 v = GLOBAL ? Cx<T2>::ldcg(&rho[e]) : rho[e];
+    if (conj) v.y = -v.y;
+    x[l] = v;
+  }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     T2 acc = Cx<T2>::zero();
 #pragma unroll
-    for (int j = 0; j < D; ++j) Cx<T2>::fma(acc, sS[i * D + j], x[j]);
-    rho[base + p.off[i]] = acc;
+    for (int j = 0; j < D; ++j) {
+      const T2 sv = sS[i * D + j];
+      if (sizeof(T2) == 16 && sv.x == 0 && sv.y == 0) continue;
+      Cx<T2>::fma(acc, sv, x[j]);
+    }
+    if (HERM) {
+      const unsigned int r = rb + (unsigned int)(p.off[i] & rmask), c = cb + (unsigned int)(p.off[i] >> p.n);
+      if (r <= c) {
+        rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+      } else if (!self) {  // a self-conjugate group writes its upper entries only
+        acc.y = -acc.y;
+        rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+      }
+    } else {
+      rho[base + p.off[i]] = acc;
+    }
   }
 }
 
@@ -115,8 +154,10 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
   __syncthreads();
 }
 
-template <typename T2>
-__global__ void __launch_bounds__(kThreads) k_batch_apply(char* arena, const BJob* __restrict__ jobs,
+// RES_HERM / TILE_HERM: resident / tile items use Hermitian mode (must match
+// BJob::herm as set by batch_herm: FP64 <true, true>, split <true, false>).
+template <typename T2, bool RES_HERM, bool TILE_HERM>
+__global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const BJob* __restrict__ jobs,
                                                           const BBlk* __restrict__ blks,
                                                           const BItem* __restrict__ items, int n_items,
                                                           int* counters, int* ticket, int* err, long long max_spin) {
@@ -142,11 +183,12 @@ __global__ void __launch_bounds__(kThreads) k_batch_apply(char* arena, const BJo
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
         stage_block(&blks[jb.block0 + b], &s_blk, sS);
         const ApplyParams& p = s_blk.p;
-        for (unsigned long long g = threadIdx.x; g < p.n_groups; g += blockDim.x) {
+        const unsigned long long total = RES_HERM ? p.n_canon : p.n_groups;
+        for (unsigned long long g = threadIdx.x; g < total; g += blockDim.x) {
           if (p.width == 1)
-            apply_group<T2, 1, false>(sR, g, p, sS);
+            apply_group<T2, 1, false, RES_HERM>(sR, g, p, sS);
           else
-            apply_group<T2, 2, false>(sR, g, p, sS);
+            apply_group<T2, 2, false, RES_HERM>(sR, g, p, sS);
         }
         __syncthreads();
       }
@@ -156,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_apply(char* arena, const BJo
     }
     // tile item: wait until every tile of the previous block of this job is done
     if (threadIdx.x == 0 && it.block > 0) {
-      const int need = jb.never_ready ? 0x7fffffff : it.block << (2 * n - jb.tile_log2);
+      const int need = jb.never_ready ? 0x7fffffff : blks[jb.block0 + it.block].tile_prefix;
       long long spins = 0;
       while (ld_acquire(&counters[it.job]) < need) {
         if (ld_acquire(err) != 0) break;
@@ -171,13 +213,14 @@ __global__ void __launch_bounds__(kThreads) k_batch_apply(char* arena, const BJo
     const ApplyParams& p = s_blk.p;
     if (*(volatile int*)err == 0) {
       const unsigned long long gpt = 1ull << (jb.tile_log2 - 2 * p.width);  // groups per tile
+      const unsigned long long total = TILE_HERM ? p.n_canon : p.n_groups;
       const unsigned long long g0 = (unsigned long long)it.tile0 * gpt;
-      const unsigned long long g1 = min(p.n_groups, g0 + (unsigned long long)it.ntiles * gpt);
+      const unsigned long long g1 = min(total, g0 + (unsigned long long)it.ntiles * gpt);
       for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
         if (p.width == 1)
-          apply_group<T2, 1, true>(rho, g, p, sS);
+          apply_group<T2, 1, true, TILE_HERM>(rho, g, p, sS);
         else
-          apply_group<T2, 2, true>(rho, g, p, sS);
+          apply_group<T2, 2, true, TILE_HERM>(rho, g, p, sS);
       }
     }
     __syncthreads();
@@ -239,6 +282,29 @@ inline size_t apply_smem() {
 
 inline bool is_resident(int n, int prec) {
   return (size_t)(prec == 0 ? 16 : 8) << (2 * n) <= (size_t)kResidentBytes;
+}
+
+// Hermitian mode in the batch kernel: every FP64 job (DFMA-bound, so the
+// transposed reads cost little); split jobs only when resident in shared
+// memory (their global passes are HBM-bound and keep full coalesced updates).
+inline bool batch_herm(int n, int prec) { return prec == 0 || is_resident(n, prec); }
+
+// Fill the per-block tile counts and wait targets of one job's blocks and
+// return its total tile count. gpt = 2^(tile_log2 - 2w) groups per tile.
+inline long long set_tiles(BBlk* blks, int n_blocks, int tile_log2, bool herm) {
+  long long prefix = 0;
+  for (int b = 0; b < n_blocks; ++b) {
+    ApplyParams& p = blks[b].p;
+    const unsigned long long M = 1ull << (p.n - p.width);
+    p.herm = herm ? 1 : 0;
+    p.n_canon = M * (M + 1) / 2;
+    const unsigned long long total = herm ? p.n_canon : p.n_groups;
+    const unsigned long long gpt = 1ull << (tile_log2 - 2 * p.width);
+    blks[b].tiles = (int)((total + gpt - 1) / gpt);
+    blks[b].tile_prefix = (int)prefix;
+    prefix += blks[b].tiles;
+  }
+  return prefix;
 }
 
 }  // namespace batch

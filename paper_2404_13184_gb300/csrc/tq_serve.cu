@@ -224,11 +224,11 @@ tq_status tq_server_create(int precision, void* cuda_stream, size_t rho_budget_b
     s->tab_mem.cap = s->tab_budget;
     const size_t smem = precision == TQ_FP64 ? apply_smem<double2>() : apply_smem<float2>();
     if (precision == TQ_FP64) {
-      e = cudaFuncSetAttribute(k_batch_apply<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<double2>, kThreads, smem);
+      e = cudaFuncSetAttribute(k_batch_apply<double2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<double2, true, true>, kThreads, smem);
     } else {
-      e = cudaFuncSetAttribute(k_batch_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2>, kThreads, smem);
+      e = cudaFuncSetAttribute(k_batch_apply<float2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2, true, false>, kThreads, smem);
     }
   }
   if (e != cudaSuccess) {
@@ -317,6 +317,7 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
     j.block0 = (int)blks.size();
     j.tile_log2 = std::min(std::max({std::min(2 * r.n, 16), 4, 2 * r.n - 16}), 2 * r.n);
     j.resident = is_resident(r.n, s->prec) ? 1 : 0;
+    j.herm = batch_herm(r.n, s->prec) ? 1 : 0;
     j.n_masks = (int)r.masks.size();
     for (size_t m = 0; m < r.masks.size(); ++m) j.masks[m] = r.masks[m];
     const size_t esz = s->prec == TQ_FP64 ? sizeof(double2) : sizeof(float2);
@@ -328,6 +329,7 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
       bb.S = sb + (size_t)r.prog.sb_off[b] * esz;
       blks.push_back(bb);
     }
+    set_tiles(blks.data() + j.block0, cnt, j.tile_log2, j.herm != 0);
     if (cnt > 0 && j.resident) items.push_back(BItem{(int)jobs.size(), -1, 0, cnt});
     job_req.push_back(id);
     cnts.push_back(cnt);
@@ -337,7 +339,7 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
   for (int k = 0; k < max_cnt; ++k)
     for (size_t j = 0; j < jobs.size(); ++j) {
       if (jobs[j].resident || k >= cnts[j]) continue;
-      const int tiles = 1 << (2 * jobs[j].n - jobs[j].tile_log2);
+      const int tiles = blks[jobs[j].block0 + k].tiles;
       for (int t = 0; t < tiles; ++t) items.push_back(BItem{(int)j, k, t, 1});
     }
   if (!items.empty()) {
@@ -365,12 +367,12 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
     int* ticket = static_cast<int*>(s->ctl.ptr);
     const int grid = (int)std::max<size_t>(1, std::min<size_t>(items.size(), (size_t)s->num_sms * s->per_sm));
     if (s->prec == TQ_FP64)
-      k_batch_apply<double2><<<grid, kThreads, apply_smem<double2>(), s->stream>>>(
+      k_batch_apply<double2, true, true><<<grid, kThreads, apply_smem<double2>(), s->stream>>>(
           static_cast<char*>(s->rho_mem.ptr), static_cast<const BJob*>(s->djobs.ptr), static_cast<const BBlk*>(s->dblks.ptr),
           static_cast<const BItem*>(s->ditems.ptr), (int)items.size(), static_cast<int*>(s->counters.ptr), ticket,
           ticket + 32, s->max_spin);
     else
-      k_batch_apply<float2><<<grid, kThreads, apply_smem<float2>(), s->stream>>>(
+      k_batch_apply<float2, true, false><<<grid, kThreads, apply_smem<float2>(), s->stream>>>(
           static_cast<char*>(s->rho_mem.ptr), static_cast<const BJob*>(s->djobs.ptr), static_cast<const BBlk*>(s->dblks.ptr),
           static_cast<const BItem*>(s->ditems.ptr), (int)items.size(), static_cast<int*>(s->counters.ptr), ticket,
           ticket + 32, s->max_spin);

@@ -22,7 +22,7 @@ def _requests(count, seed, n_lo=2, n_hi=9):
 
 
 def _single(tq, precision, n, ops, masks):
-    with tq.State(n, precision, hermitian=False) as st:   # the server updates every group
+    with tq.State(n, precision, hermitian=precision == "fp64") as st:   # FP64: the same canonical-group arithmetic
         st.run(ops, width=2)
         tr = st.trace()
         return np.concatenate([[tr.real, tr.imag], st.expect_z(masks)])
