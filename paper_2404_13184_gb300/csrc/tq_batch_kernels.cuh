@@ -88,9 +88,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 // through L2 only (other CTAs wrote it); else rho is the shared-memory copy.
 // HERM: t indexes the canonical groups (row rest <= column rest); entries
 // below the diagonal are read and written through their conjugate
-// transposes, as in the single-state kernels. FP64 skips exactly-zero
-// superoperator entries: S is the same for every thread, so the branch is
-// uniform, and the result is unchanged (an FMA with a zero product is exact).
+// transposes, as in the single-state kernels. Used for split states; FP64
+// blocks go through the row-list forms below.
 template <typename T2, int K, bool GLOBAL, bool HERM>
 __device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const ApplyParams& p, const T2* sS) {
   constexpr int D = 1 << (2 * K);
@@ -125,11 +124,7 @@ __device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const
   for (int i = 0; i < D; ++i) {
     T2 acc = Cx<T2>::zero();
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const T2 sv = sS[i * D + j];
-      if (sizeof(T2) == 16 && sv.x == 0 && sv.y == 0) continue;
-      Cx<T2>::fma(acc, sv, x[j]);
-    }
+    for (int j = 0; j < D; ++j) Cx<T2>::fma(acc, sS[i * D + j], x[j]);
     if (HERM) {
       const unsigned int r = rb + (unsigned int)(p.off[i] & rmask), c = cb + (unsigned int)(p.off[i] >> p.n);
       if (r <= c) {
@@ -144,13 +139,156 @@ __device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const
   }
 }
 
+// Row lists of an FP64 superoperator in shared memory: the nonzeros of row
+// i are val[k], column col[k], for k in [rowptr[i], rowptr[i+1]). FP64
+// applies are bound by the FP64 pipe, so only nonzero products are issued;
+// the loops run over these lists (a data-dependent trip count, so the
+// compiler cannot turn skipped products into predicated ones), and the
+// result is that of the dense product (an FMA with a zero product is exact).
+struct RowLists {
+  int rowptr[17];
+  unsigned char col[kSEntries];
+};
+static_assert(16 * kThreads * 16 <= kResidentBytes, "operand columns of a width-2 FP64 tile item");
+
+// FP64 tile items: gather the group's 4^K entries (through L2: other CTAs
+// wrote them) into this thread's shared-memory column mine[l * kThreads],
+// then each output is a row-list dot product, written back in place.
+template <int K, bool HERM>
+__device__ __forceinline__ void apply_group_lists_global(double2* rho, unsigned long long t, const ApplyParams& p,
+                                                         const double2* val, const RowLists& rl, double2* mine) {
+  constexpr int D = 1 << (2 * K);
+  bool self = false;
+  unsigned long long base = HERM ? canonical_group(t, p.n - K, &self) : t;
+#pragma unroll
+  for (int i = 0; i < 2 * K; ++i) {
+    const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
+    base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
+  }
+  const unsigned int rmask = (1u << p.n) - 1u;
+  const unsigned int rb = (unsigned int)(base & rmask), cb = (unsigned int)(base >> p.n);
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    unsigned long long e;
+    bool conj = false;
+    if (HERM) {
+      const unsigned int r = rb + (unsigned int)(p.off[l] & rmask), c = cb + (unsigned int)(p.off[l] >> p.n);
+      conj = r > c;
+      e = conj ? ((unsigned long long)c | ((unsigned long long)r << p.n)) : ((unsigned long long)r | ((unsigned long long)c << p.n));
+    } else {
+      e = base + p.off[l];
+    }
+    double2 v = __ldcg(&rho[e]);
+    if (conj) v.y = -v.y;
+    mine[l * kThreads] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = rl.rowptr[i]; k < rl.rowptr[i + 1]; ++k) Cx<double2>::fma(acc, val[k], mine[rl.col[k] * kThreads]);
+    if (HERM) {
+      const unsigned int r = rb + (unsigned int)(p.off[i] & rmask), c = cb + (unsigned int)(p.off[i] >> p.n);
+      if (r <= c) {
+        rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+      } else if (!self) {
+        acc.y = -acc.y;
+        rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+      }
+    } else {
+      rho[base + p.off[i]] = acc;
+    }
+  }
+}
+
+// FP64 resident items: the operands are read from the shared-memory copy of
+// rho as the row lists name them; all 4^K outputs stay in registers until
+// the group's last read, then are stored (groups are disjoint, so no other
+// thread touches these entries).
+template <int K, bool HERM>
+__device__ __forceinline__ void apply_group_lists_resident(double2* sR, unsigned int t, const ApplyParams& p,
+                                                           const double2* val, const RowLists& rl) {
+  constexpr int D = 1 << (2 * K);
+  bool self = false;
+  unsigned int base = HERM ? (unsigned int)canonical_group(t, p.n - K, &self) : t;
+#pragma unroll
+  for (int i = 0; i < 2 * K; ++i) {
+    const unsigned int low = base & ((1u << p.pos[i]) - 1u);
+    base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
+  }
+  const unsigned int rmask = (1u << p.n) - 1u;
+  const unsigned int rb = base & rmask, cb = base >> p.n;
+  double2 out[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = rl.rowptr[i]; k < rl.rowptr[i + 1]; ++k) {
+      const unsigned int off = (unsigned int)p.off[rl.col[k]];
+      double2 v;
+      if (HERM) {
+        const unsigned int r = rb + (off & rmask), c = cb + (off >> p.n);
+        v = sR[r <= c ? (r | (c << p.n)) : (c | (r << p.n))];
+        if (r > c) v.y = -v.y;
+      } else {
+        v = sR[base + off];
+      }
+      Cx<double2>::fma(acc, val[k], v);
+    }
+    out[i] = acc;
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double2 acc = out[i];
+    const unsigned int off = (unsigned int)p.off[i];
+    if (HERM) {
+      const unsigned int r = rb + (off & rmask), c = cb + (off >> p.n);
+      if (r <= c) {
+        sR[r | (c << p.n)] = acc;
+      } else if (!self) {
+        acc.y = -acc.y;
+        sR[c | (r << p.n)] = acc;
+      }
+    } else {
+      sR[base + off] = acc;
+    }
+  }
+}
+
+// Copy a block's descriptor to shared memory with its superoperator: dense
+// (split) or as row lists (FP64; zero tests on the bit patterns, so -0.0
+// counts as zero). The row lists take rows in order, each thread i < D
+// placing row i after the counts of rows < i.
 template <typename T2>
-__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS) {
+__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl) {
   if (threadIdx.x == 0) *s_blk = *blk;
   __syncthreads();
   const int D = 1 << (2 * s_blk->p.width);
   const T2* S = static_cast<const T2*>(s_blk->S);
-  for (int e = threadIdx.x; e < D * D; e += blockDim.x) sS[e] = S[e];
+  if (sizeof(T2) == 8) {
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) sS[e] = S[e];
+  } else {
+    const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(S);
+    unsigned int m = 0;
+    if (threadIdx.x < D)
+      for (int j = 0; j < D; ++j) {
+        const int e = threadIdx.x * D + j;
+        if (((bits[2 * e] | bits[2 * e + 1]) << 1) != 0ull) m |= 1u << j;
+      }
+    if (threadIdx.x < D) rl->rowptr[threadIdx.x + 1] = __popc(m);
+    if (threadIdx.x == 0) rl->rowptr[0] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 1; i <= D; ++i) rl->rowptr[i] += rl->rowptr[i - 1];
+    __syncthreads();
+    if (threadIdx.x < D) {
+      int k = rl->rowptr[threadIdx.x];
+      for (int j = 0; j < D; ++j)
+        if ((m >> j) & 1u) {
+          sS[k] = S[threadIdx.x * D + j];
+          rl->col[k] = (unsigned char)j;
+          ++k;
+        }
+    }
+  }
   __syncthreads();
 }
 
@@ -165,7 +303,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
   T2* sS = reinterpret_cast<T2*>(smem);
   T2* sR = sS + kSEntries;
   __shared__ BBlk s_blk;
+  __shared__ RowLists s_rl;
   __shared__ int s_idx;
+  constexpr bool kF64 = sizeof(T2) == 16;
   for (;;) {
     if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
     __syncthreads();
@@ -181,14 +321,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       const int N = 1 << (2 * n);
       for (int e = threadIdx.x; e < N; e += blockDim.x) sR[e] = Cx<T2>::ldcg(&rho[e]);
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
-        stage_block(&blks[jb.block0 + b], &s_blk, sS);
+        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl);
         const ApplyParams& p = s_blk.p;
         const unsigned long long total = RES_HERM ? p.n_canon : p.n_groups;
         for (unsigned long long g = threadIdx.x; g < total; g += blockDim.x) {
-          if (p.width == 1)
-            apply_group<T2, 1, false, RES_HERM>(sR, g, p, sS);
-          else
-            apply_group<T2, 2, false, RES_HERM>(sR, g, p, sS);
+          if constexpr (kF64) {
+            double2* sR64 = reinterpret_cast<double2*>(sR);
+            const double2* val = reinterpret_cast<const double2*>(sS);
+            if (p.width == 1)
+              apply_group_lists_resident<1, RES_HERM>(sR64, (unsigned int)g, p, val, s_rl);
+            else
+              apply_group_lists_resident<2, RES_HERM>(sR64, (unsigned int)g, p, val, s_rl);
+          } else {
+            if (p.width == 1)
+              apply_group<T2, 1, false, RES_HERM>(sR, g, p, sS);
+            else
+              apply_group<T2, 2, false, RES_HERM>(sR, g, p, sS);
+          }
         }
         __syncthreads();
       }
@@ -209,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         __nanosleep(128);
       }
     }
-    stage_block(&blks[jb.block0 + it.block], &s_blk, sS);
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl);
     const ApplyParams& p = s_blk.p;
     if (*(volatile int*)err == 0) {
       const unsigned long long gpt = 1ull << (jb.tile_log2 - 2 * p.width);  // groups per tile
@@ -217,10 +366,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       const unsigned long long g0 = (unsigned long long)it.tile0 * gpt;
       const unsigned long long g1 = min(total, g0 + (unsigned long long)it.ntiles * gpt);
       for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-        if (p.width == 1)
-          apply_group<T2, 1, true, TILE_HERM>(rho, g, p, sS);
-        else
-          apply_group<T2, 2, true, TILE_HERM>(rho, g, p, sS);
+        if constexpr (kF64) {
+          // the resident buffer is free in tile items: it holds the
+          // threads' operand columns (16 x kThreads entries = 64 KiB)
+          double2* mine = reinterpret_cast<double2*>(sR) + threadIdx.x;
+          const double2* val = reinterpret_cast<const double2*>(sS);
+          double2* rho64 = reinterpret_cast<double2*>(rho);
+          if (p.width == 1)
+            apply_group_lists_global<1, TILE_HERM>(rho64, g, p, val, s_rl, mine);
+          else
+            apply_group_lists_global<2, TILE_HERM>(rho64, g, p, val, s_rl, mine);
+        } else {
+          if (p.width == 1)
+            apply_group<T2, 1, true, TILE_HERM>(rho, g, p, sS);
+          else
+            apply_group<T2, 2, true, TILE_HERM>(rho, g, p, sS);
+        }
       }
     }
     __syncthreads();

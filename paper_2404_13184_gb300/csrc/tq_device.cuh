@@ -84,7 +84,10 @@ struct SparseWork {
 // column: t = b (b + 1) / 2 + a); rest_bits = n - width.
 __host__ __device__ __forceinline__ unsigned long long canonical_group(unsigned long long t, int rest_bits,
                                                                        bool* self) {
-  unsigned long long b = (unsigned long long)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  // FP32 estimate (off by at most one for t < 2^31), corrected exactly in
+  // integers; the FP64 pipe stays free for the apply arithmetic.
+  const float est = (sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f;
+  unsigned long long b = est > 0.0f ? (unsigned long long)est : 0ull;
   while (b * (b + 1) / 2 > t) --b;
   while ((b + 1) * (b + 2) / 2 <= t) ++b;
   const unsigned long long a = t - b * (b + 1) / 2;
