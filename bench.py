@@ -306,12 +306,25 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, oracle_sample=12,
                       abs(results[j][3] - dm_oracle.expect_z(rho, 3) / norm))
         err = {"circuits_checked": len(small), "max_abs_trace_err": e_tr, "max_abs_z_err": e_z}
     info = b.info()
+    work = b.work()
     b.free()
+    # roofline of the whole run (graph replay incl. superoperator build, fusion
+    # and readout): FP64 against the DFMA rate, split against HBM bandwidth
+    hbm_gbs, sm_max, src = peaks()
+    if precision == "fp64":
+        ach = work["flops"] / (ms / 1e3) / 1e12
+        peak = fp64_peak_tflops(sm_max)
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "flops_per_run": work["flops"], "peak_source": "DFMA pipe: 152 SMs x 4 FP64 flop/clk x SM max clock"}
+    else:
+        ach = work["bytes"] / (ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
+                "bytes_per_run": work["bytes"], "peak_source": f"hbm_gbs ({src})"}
     gates = sum(c.n_gates for c in circuits)
     return {"ms_per_run": ms, "circuits_per_s": count / (ms / 1e3), "gates_per_s": gates / (ms / 1e3),
             "circuits": count, "noisy_gates": gates, "items": info["items"], "rho_bytes": info["rho_bytes"],
             "autotune": {str(n): {"tile_log2": t, "width": w, "ms": round(m, 3)} for n, (t, w, m) in tuned.items()},
-            "autotune_s": t_tune, "oracle_check": err, "results": results}
+            "autotune_s": t_tune, "oracle_check": err, "roofline": roof, "results": results}
 
 
 def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=150 << 30, max_live=64):

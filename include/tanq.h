@@ -295,6 +295,17 @@ tq_status tq_batch_get_rho(tq_batch* b, int job, double* out);
 /* Jobs, work items of the persistent launch, bytes of all density matrices. */
 tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size_t* rho_bytes);
 
+/* Algorithmic work of one run, counted on the device from the fused
+ * superoperators of the last run (Sec. 3.1: one gather, product and scatter
+ * per group). flops: 8 real flops per complex multiply-add the apply kernel
+ * issues, over every block's groups (canonical groups in Hermitian mode);
+ * FP64 counts nonzero superoperator entries only (its row lists skip the
+ * zeros), split counts all. bytes: what the apply passes must move through
+ * HBM: per block of a tile job one read and one write of the stored entries
+ * (the upper triangle in Hermitian mode), per resident job one load and one
+ * store of vec(rho). TQ_ERR_STATE before the first run; waits for the run. */
+tq_status tq_batch_work(tq_batch* b, double* flops, double* bytes);
+
 void tq_batch_free(tq_batch* b);
 
 /* Autotuner of the batch engine: times every (fusion width in {1, 2},

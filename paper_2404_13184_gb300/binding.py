@@ -85,6 +85,7 @@ _SIGNATURES = [
     ("tq_batch_result", c_int, [c_void_p, c_int, POINTER(c_double)]),
     ("tq_batch_get_rho", c_int, [c_void_p, c_int, POINTER(c_double)]),
     ("tq_batch_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_size_t)]),
+    ("tq_batch_work", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     ("tq_batch_free", None, [c_void_p]),
     ("tq_autotune", c_int, [c_int, c_int, ctypes.c_char_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
     ("tq_server_create", c_int, [c_int, c_void_p, c_size_t, c_size_t, c_int, POINTER(c_void_p)]),
@@ -250,6 +251,12 @@ class Batch:
         a, b, c = c_size_t(0), c_size_t(0), c_size_t(0)
         _check(_lib.tq_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tq_batch_info")
         return {"jobs": a.value, "items": b.value, "rho_bytes": c.value}
+
+    def work(self) -> dict:
+        """Algorithmic flops and HBM bytes of one run (after a run)."""
+        f, by = c_double(), c_double()
+        _check(_lib.tq_batch_work(self._h, ctypes.byref(f), ctypes.byref(by)), "tq_batch_work")
+        return {"flops": f.value, "bytes": by.value}
 
     def free(self):
         if self._h:

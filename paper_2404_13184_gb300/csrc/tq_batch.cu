@@ -70,6 +70,33 @@ int default_tile_log2(int n, int prec) {
 }
 
 
+// Algorithmic flops and HBM bytes of one run (see tq_batch_work): one CTA
+// per job, threads over its blocks; FP64 counts the nonzeros of S by their
+// bit patterns, as the row-list staging does.
+__global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restrict__ blks, int prec,
+                             unsigned long long* __restrict__ out) {
+  const BJob& jb = jobs[blockIdx.x];
+  const unsigned long long esz = prec == 0 ? 16 : 8;
+  const unsigned long long N = 1ull << (2 * jb.n), R = 1ull << jb.n;
+  unsigned long long fl = 0, by = 0;
+  for (int b = threadIdx.x; b < jb.n_blocks; b += blockDim.x) {
+    const BBlk& bk = blks[jb.block0 + b];
+    const int D = 1 << (2 * bk.p.width);
+    unsigned long long nnz = (unsigned long long)D * D;
+    if (prec == 0) {
+      const unsigned long long* bits = static_cast<const unsigned long long*>(bk.S);
+      nnz = 0;
+      for (int e = 0; e < D * D; ++e) nnz += ((bits[2 * e] | bits[2 * e + 1]) << 1) != 0ull;
+    }
+    const unsigned long long groups = jb.herm ? bk.p.n_canon : bk.p.n_groups;
+    fl += 8ull * nnz * groups;
+    if (!jb.resident) by += (jb.herm ? N + R : 2 * N) * esz;
+  }
+  if (jb.resident && threadIdx.x == 0 && jb.n_blocks > 0) by += 2 * N * esz;
+  atomicAdd(&out[0], fl);
+  atomicAdd(&out[1], by);
+}
+
 void drop_graph(tq_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -387,6 +414,30 @@ tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size
   if (n_jobs) *n_jobs = b->jobs.size();
   if (n_items) *n_items = b->n_items;
   if (rho_bytes) *rho_bytes = b->arena_bytes;
+  return TQ_OK;
+}
+
+tq_status tq_batch_work(tq_batch* b, double* flops, double* bytes) {
+  if (!b) return TQ_ERR_ARG;
+  if (!b->ready) return TQ_ERR_STATE;
+  tq_status st = tq_batch_wait(b);
+  if (st != TQ_OK) return st;
+  unsigned long long h[2] = {0, 0};
+  DevBuf tmp;
+  cudaError_t e = alloc(tmp, sizeof(h));
+  if (e == cudaSuccess) e = cudaMemsetAsync(tmp.ptr, 0, sizeof(h), b->stream);
+  if (e == cudaSuccess) {
+    k_batch_work<<<(unsigned)b->jobs.size(), 256, 0, b->stream>>>(static_cast<const BJob*>(b->djobs.ptr),
+                                                                  static_cast<const BBlk*>(b->dblks.ptr), b->prec,
+                                                                  static_cast<unsigned long long*>(tmp.ptr));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, tmp.ptr, sizeof(h), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (tmp.ptr) cudaFree(tmp.ptr);
+  if (e != cudaSuccess) return to_status(e);
+  if (flops) *flops = (double)h[0];
+  if (bytes) *bytes = (double)h[1];
   return TQ_OK;
 }
 

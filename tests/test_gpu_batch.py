@@ -49,6 +49,64 @@ def test_batch_matches_oracle_and_replays(tq, precision):
     b.free()
 
 
+def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
+    """Flops and HBM bytes tq_batch_work must report for one job, from the
+    plan's block widths: FP64 jobs and resident split jobs run canonical
+    groups; FP64 counts nonzeros (a diagonal block has D of them)."""
+    esz = 16 if precision == "fp64" else 8
+    resident = esz * 4 ** n <= 64 * 1024
+    herm = precision == "fp64" or resident
+    _, widths = tq.plan_fusion(n, ops, width, precision)
+    flops = bytes_ = 0
+    for w in widths:
+        M = 2 ** (n - w)
+        groups = M * (M + 1) // 2 if herm else 4 ** (n - w)
+        nnz = 4 ** w if (precision == "fp64" and diagonal_fp64) else 16 ** w
+        flops += 8 * nnz * groups
+        if not resident:
+            bytes_ += ((4 ** n + 2 ** n) if herm else 2 * 4 ** n) * esz
+    if resident and widths:
+        bytes_ += 2 * 4 ** n * esz
+    return flops, bytes_
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("width", [1, 2])
+def test_batch_work_counts(tq, precision, width):
+    # diagonal circuits (RZ, CZ, RZZ): every fused FP64 block has exactly D
+    # nonzeros, so the device count is known in closed form; split counts
+    # dense products. Resident (n <= 6) and tile (7, 8) jobs.
+    rng = np.random.default_rng(7)
+    jobs = []
+    for n in (3, 6, 7, 8):
+        ops = []
+        for _ in range(30):
+            if rng.random() < 0.5:
+                ops.append(("rz", [int(rng.integers(n))], (float(rng.uniform(-3, 3)),)))
+            else:
+                a, c = (int(v) for v in rng.choice(n, 2, replace=False))
+                ops.append(("cz", [a, c], ()) if rng.random() < 0.5 else ("rzz", [a, c], (float(rng.uniform(-3, 3)),)))
+        jobs.append((n, ops))
+    b = tq.Batch(precision)
+    with pytest.raises(tq.TqError):
+        b.work()                      # nothing has run yet
+    for n, ops in jobs:
+        b.add(n, ops, width=width)
+    b.run()
+    b.wait()
+    want_f = want_b = 0
+    for n, ops in jobs:
+        f, by = _expected_work(tq, precision, n, ops, width, diagonal_fp64=True)
+        want_f += f
+        want_b += by
+    got = b.work()
+    assert got["flops"] == want_f and got["bytes"] == want_b
+    for j, (n, ops) in enumerate(jobs):
+        tol = TOL64 if precision == "fp64" else 2e-6
+        assert np.max(np.abs(b.rho(j) - O.run_circuit(n, ops))) < tol
+    b.free()
+
+
 def test_batch_job_alone_equals_in_mix_and_single_state(tq):
     jobs = _jobs(40, 4, 9, 2, depth=(20, 60))
     mix = tq.Batch("fp64")
