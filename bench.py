@@ -391,6 +391,86 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
             "sustainable_rate_per_s": len(lat) / max(busy, 1e-9)}
 
 
+def run_plain6(tq, torch, steps, warmup):
+    """6 qubits, 200 random noisy gates, FP64, no fusion (every gate and
+    every channel is its own pass): the single-state device program (one
+    launch per pass) and the batch engine (one resident CTA for the whole
+    circuit, one persistent launch), per circuit run, with the oracle error
+    of <Z_i>."""
+    from paper_2404_13184_gb300 import workloads
+    c = workloads.plain_6q()
+    out = {"noisy_gates": c.n_gates, "ops": len(c.ops)}
+    st = tq.State(c.n, "fp64")
+    prog = tq.DeviceProgram(c.n, c.ops, 0, "fp64")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, warmup)):
+        st.reset()
+        st.run_program(prog)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        st.reset()
+        st.run_program(prog)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    z_gpu = list(st.expect_z([1 << q for q in range(c.n)]))
+    out["program"] = {"ms_per_circuit": ms, "gates_per_s": c.n_gates / (ms / 1e3), "passes": prog.n_blocks}
+    st.free()
+    b = tq.Batch("fp64")
+    b.add(c.n, c.ops, width=0, masks=[1 << q for q in range(c.n)])
+    for _ in range(max(1, warmup)):
+        b.run()
+        b.wait()
+    e0.record(stream)
+    for _ in range(steps):
+        b.run()
+    e1.record(stream)
+    b.wait()
+    ms = e0.elapsed_time(e1) / steps
+    z_b = list(b.result(0)[2:])
+    b.free()
+    out["batch_engine"] = {"ms_per_circuit": ms, "gates_per_s": c.n_gates / (ms / 1e3)}
+    from oracle import dm_oracle
+    rho = dm_oracle.run_circuit(c.n, c.ops)
+    z_o = [dm_oracle.expect_z(rho, 1 << q) for q in range(c.n)]
+    out["oracle_check"] = {"max_abs_z_err_program": max(abs(a - b) for a, b in zip(z_gpu, z_o)),
+                           "max_abs_z_err_batch": max(abs(a - b) for a, b in zip(z_b, z_o))}
+    return out
+
+
+def run_teleport(tq, precision):
+    """Teleportation channel tomography (Sec. 5, Case Study-1) for the
+    noiseless, device-like and 0.1-gate-error settings."""
+    from paper_2404_13184_gb300 import case_studies as C
+    names = ["noiseless", "device", "device_gate_error_0.1"]
+    chis, _, ms = C.teleport_chi(tq, [C.NOISELESS, C.DEVICE, C.DEVICE_WORSE], precision)
+    return {"batch_ms": ms, "jobs": 36, "settings": {
+        nm: {"process_fidelity": C.process_fidelity(chi),
+             "chi_re": [[round(float(v), 6) for v in row] for row in chi.real],
+             "chi_im": [[round(float(v), 6) for v in row] for row in chi.imag]} for nm, chi in zip(names, chis)}}
+
+
+def run_purify(tq, precision):
+    """Two rounds of nested purification (Sec. 5, Case Study-2): output
+    fidelity against input Werner fidelity for several CX error rates, and
+    the band of inputs that purification improves."""
+    from paper_2404_13184_gb300 import case_studies as C
+    Fs = [round(0.5 + 0.025 * i, 3) for i in range(21)]
+    ps = [0.0, 0.01, 0.03, 0.05, 0.07, 0.1]
+    curves, ms = C.purification_curves(tq, Fs, ps, 2, precision)
+    out = {"batch_ms": ms, "jobs": len(Fs) * len(ps), "qubits": 8, "curves": {}}
+    for p in ps:
+        better = [F for F, f, _ in curves[p] if f > F + 1e-12]
+        out["curves"][str(p)] = {"F_out": [round(f, 6) for _, f, _ in curves[p]],
+                                 "P_success": [round(s_, 6) for _, _, s_ in curves[p]],
+                                 "improves_for_F_in": [min(better), max(better)] if better else None}
+    out["F_in"] = Fs
+    return out
+
+
 def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12):
     """Layered thermal-relaxation workload (n = 12: 2^24 entries, 2000 gates):
     time of the whole circuit per fusion width (0 = unfused plain path) and
@@ -463,7 +543,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None, help="timed steps of the FP64 leg (default --steps)")
     ap.add_argument("--n-qubits", type=int, default=15, help="register size (15 for the benchmark; smaller "
                     "registers for profiling captures)")
-    ap.add_argument("--workload", default="tfim15", choices=["tfim15", "sweep", "serve", "layered12"],
+    ap.add_argument("--workload", default="tfim15",
+                    choices=["tfim15", "sweep", "serve", "layered12", "plain6", "teleport", "purify"],
                     help="tfim15: the benchmark line; sweep / serve: the batched-sweep and served-stream workloads")
     ap.add_argument("--precision", default="both", choices=["fp64", "split", "both"], help="sweep / serve modes")
     ap.add_argument("--sweep-count", type=int, default=1024)
@@ -503,6 +584,20 @@ def main():
                 print(json.dumps({"metric": "layered thermal circuit: time per fusion width", "workload":
                                   "layered-thermal-12q-2000g", "dtype": "f64" if prec == "fp64" else "f32", **r}),
                       flush=True)
+        return 0
+    if args.workload == "plain6":
+        r = run_plain6(tq, torch, max(args.steps, 20), args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": "plain 6-qubit circuit, unfused: noisy gates/s", "workload":
+                              "plain-6q-200g (FP64, no fusion)", "dtype": "f64", **r}), flush=True)
+        return 0
+    if args.workload in ("teleport", "purify"):
+        precs = ["fp64", "split"] if args.precision == "both" else [args.precision]
+        for prec in precs:
+            r = run_teleport(tq, prec) if args.workload == "teleport" else run_purify(tq, prec)
+            if rank == 0:
+                print(json.dumps({"metric": f"case study: {args.workload}", "dtype": "f64" if prec == "fp64" else "f32",
+                                  **r}), flush=True)
         return 0
     if args.workload in ("sweep", "serve"):
         precs = ["fp64", "split"] if args.precision == "both" else [args.precision]

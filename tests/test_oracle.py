@@ -378,3 +378,44 @@ def test_readout_and_sampling():
     assert abs(np.sum(O.readout_probabilities(np.full(8, 1 / 8), [0.1] * 3, [0.2] * 3)) - 1) < 1e-15
     assert list(O.sample([0.5, 0.0, 0.25, 0.25], [0.1, 0.49, 0.5, 0.74, 0.76, 0.999])) == [0, 0, 2, 2, 3, 3]
     assert list(O.sample(np.eye(4)[2], [0.0, 0.5, 0.9999])) == [2, 2, 2]
+
+
+# ------------------------------------------------- case studies (Sec. 5)
+
+def _dejmps(A, B, C, D):
+    # Deutsch et al. (1996): Bell-diagonal weights (Phi+, Psi-, Psi+, Phi-)
+    # after one successful round, and the success probability
+    N = (A + B) ** 2 + (C + D) ** 2
+    return ((A * A + B * B) / N, 2 * C * D / N, (C * C + D * D) / N, 2 * A * B / N), N
+
+
+@pytest.mark.parametrize("rounds", [1, 2])
+@pytest.mark.parametrize("F", [0.55, 0.7, 0.9])
+def test_purification_matches_dejmps_recurrence(rounds, F):
+    from paper_2404_13184_gb300 import case_studies as C
+    n, ops = C.purification_ops(F, 0.0, rounds)
+    rho = O.run_circuit(n, ops)
+    tr = O.trace(rho).real
+    # after the Bell-basis change |Phi+> -> |00> on qubits 0, 1
+    p00 = sum(rho[x, x].real for x in range(1 << n) if x & 3 == 0)
+    w, succ = _dejmps(F, (1 - F) / 3, (1 - F) / 3, (1 - F) / 3)
+    if rounds == 2:
+        # two independent first-round successes, then the second round
+        w, N2 = _dejmps(*w)
+        succ = succ * succ * N2
+    assert abs(p00 / tr - w[0]) < 1e-13
+    assert abs(tr - succ) < 1e-13
+
+
+@pytest.mark.parametrize("e10,e01", [(0.02, 0.02), (0.02, 0.06), (0.1, 0.0)])
+def test_teleportation_readout_error_is_a_pauli_channel(e10, e01):
+    # every Bell-measurement outcome has probability 1/4 whatever the input,
+    # so each recorded bit is flipped with probability e = (e10 + e01)/2,
+    # independently: a wrong m1 leaves an X error, a wrong m0 a Z error
+    from paper_2404_13184_gb300 import case_studies as C
+    noise = C.DeviceNoise(e10=e10, e01=e01)
+    chan = lambda E: _teleport_channel(E, C.teleport_ops(noise, [], []))
+    chi = _chi_matrix(chan)
+    e = (e10 + e01) / 2
+    want = np.diag([(1 - e) ** 2, e * (1 - e), e * e, e * (1 - e)])
+    assert np.max(np.abs(chi - want)) < 1e-13
