@@ -376,7 +376,7 @@ def test_hermitian_mode_follows_set_rho(tq):
 
 
 @pytest.mark.parametrize("width", [0, 1, 2, 3, -1])
-@pytest.mark.parametrize("n", [5, 6, 9])
+@pytest.mark.parametrize("n", [5, 6, 9, 11])
 def test_split_hermitian_mode_matches_oracle(tq, n, width):
     # split Hermitian mode runs widths 1-2 through coalesced 16 x 16 group
     # tiles (direct or transposed per local index); width-3 blocks in the mix
