@@ -162,7 +162,7 @@ tq_status finalize(tq_batch* b) {
       bb.S = reinterpret_cast<const void*>(J.prog.sb_off[k] + sbb);  // offset; made absolute below
       hblks.push_back(bb);
     }
-    if (set_tiles(hblks.data() + hj.block0, hj.n_blocks, hj.tile_log2, hj.herm != 0) >= (1ll << 31))
+    if (set_tiles(hblks.data() + hj.block0, hj.n_blocks, hj.tile_log2, hj.herm != 0, tiled16_job(J.n, b->prec)) >= (1ll << 31))
       return TQ_ERR_UNSUPPORTED;
     arena = align_up(arena + ((size_t)(b->prec == TQ_FP64 ? 16 : 8) << (2 * J.n)), 256);
   }
@@ -236,8 +236,8 @@ tq_status finalize(tq_batch* b) {
     e = cudaFuncSetAttribute(k_batch_apply<double2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<double2, true, true>, kThreads, smem);
   } else {
-    e = cudaFuncSetAttribute(k_batch_apply<float2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<float2, true, false>, kThreads, smem);
+    e = cudaFuncSetAttribute(k_batch_apply<float2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<float2, true, true>, kThreads, smem);
   }
   if (e != cudaSuccess) return to_status(e);
   b->per_sm = std::max(1, b->per_sm);
@@ -274,7 +274,7 @@ tq_status finalize(tq_batch* b) {
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
     else
-      k_batch_apply<float2, true, false><<<grid, kThreads, smem, st>>>(
+      k_batch_apply<float2, true, true><<<grid, kThreads, smem, st>>>(
           static_cast<char*>(b->arena.ptr), static_cast<const BJob*>(b->djobs.ptr),
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);

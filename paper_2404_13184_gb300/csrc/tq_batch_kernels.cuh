@@ -151,6 +151,29 @@ struct RowLists {
 };
 static_assert(16 * kThreads * 16 <= kResidentBytes, "operand columns of a width-2 FP64 tile item");
 
+// Split tile items in Hermitian mode walk the canonical groups in 16 x 16
+// tiles of (row rest a, column rest b), one group per thread: thread (i, j)
+// takes a = 16 ta + i, b = 16 tb + j. Rows are dep(16 ta) + dep16[i] + rt[l]
+// (dep inserts zeros at the target qubits and is additive over disjoint
+// bits), columns likewise; consecutive threads take consecutive rows, so
+// entries above the diagonal are read and written coalesced, and the
+// transposed entries below it share 32-byte sectors with the neighbouring
+// warps of the same tile.
+struct Tile16 {
+  unsigned dep16[16];
+  unsigned rt[16], ct[16];  // row / column target bits of local index l
+  int qs[2];                // target qubits ascending
+};
+static_assert(kThreads == 256, "one 16 x 16 tile of groups per CTA pass");
+
+// Canonical 16 x 16 tiles per work item of a split Hermitian tile job: the
+// same entries per item as 2^(tile_log2 - 2w) groups (a tile holds 2^8).
+__host__ __device__ inline int tiles16_log2(int tile_log2, int width) {
+  const int v = tile_log2 - 2 * width - 8;
+  return v > 0 ? v : 0;
+}
+
+
 // FP64 tile items: gather the group's 4^K entries (through L2: other CTAs
 // wrote them) into this thread's shared-memory column mine[l * kThreads],
 // then each output is a row-list dot product, written back in place.
@@ -253,18 +276,76 @@ __device__ __forceinline__ void apply_group_lists_resident(double2* sR, unsigned
   }
 }
 
+// One canonical 16 x 16 tile u of a width-K split block (see Tile16).
+template <int K>
+__device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, const ApplyParams& p,
+                                             const float2* sS, const Tile16& t) {
+  constexpr int D = 1 << (2 * K);
+  const int i = threadIdx.x % 16, j = threadIdx.x / 16;
+  bool diag = false;
+  const unsigned long long tt = canonical_group(u, 32, &diag);  // (ta, tb) as ta | tb << 32
+  if (diag && i > j) return;  // not a canonical group
+  const bool self = diag && i == j;
+  const unsigned rbase = (unsigned)deposit_zeros((tt & 0xffffffffull) * 16, t.qs, K) + t.dep16[i];
+  const unsigned cbase = (unsigned)deposit_zeros((tt >> 32) * 16, t.qs, K) + t.dep16[j];
+  float2 x[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const unsigned r = rbase + t.rt[l], c = cbase + t.ct[l];
+    const bool up = r <= c;
+    float2 v = __ldcg(&rho[up ? ((unsigned long long)r | ((unsigned long long)c << p.n))
+                              : ((unsigned long long)c | ((unsigned long long)r << p.n))]);
+    if (!up) v.y = -v.y;
+    x[l] = v;
+  }
+#pragma unroll
+  for (int o = 0; o < D; ++o) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int l = 0; l < D; ++l) Cx<float2>::fma(acc, sS[o * D + l], x[l]);
+    const unsigned r = rbase + t.rt[o], c = cbase + t.ct[o];
+    if (r <= c) {
+      rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+    } else if (!self) {  // a self-conjugate group writes its upper entries only
+      acc.y = -acc.y;
+      rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+    }
+  }
+}
+
 // Copy a block's descriptor to shared memory with its superoperator: dense
 // (split) or as row lists (FP64; zero tests on the bit patterns, so -0.0
 // counts as zero). The row lists take rows in order, each thread i < D
 // placing row i after the counts of rows < i.
 template <typename T2>
-__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl) {
+__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl, Tile16* t16) {
   if (threadIdx.x == 0) *s_blk = *blk;
   __syncthreads();
   const int D = 1 << (2 * s_blk->p.width);
   const T2* S = static_cast<const T2*>(s_blk->S);
   if (sizeof(T2) == 8) {
     for (int e = threadIdx.x; e < D * D; e += blockDim.x) sS[e] = S[e];
+    const ApplyParams& p = s_blk->p;
+    const int K = p.width;
+    if (threadIdx.x < 16) {
+      int qs[2] = {p.q[0], K == 2 ? p.q[1] : 0};
+      if (K == 2 && qs[0] > qs[1]) {
+        const int t = qs[0];
+        qs[0] = qs[1];
+        qs[1] = t;
+      }
+      t16->dep16[threadIdx.x] = (unsigned)deposit_zeros((unsigned long long)threadIdx.x, qs, K);
+      if (threadIdx.x < 2) t16->qs[threadIdx.x] = qs[threadIdx.x];
+      if (threadIdx.x < D) {
+        unsigned rt = 0, ct = 0;
+        for (int j = 0; j < K; ++j) {
+          rt |= ((threadIdx.x >> j) & 1u) << p.q[j];
+          ct |= ((threadIdx.x >> (K + j)) & 1u) << p.q[j];
+        }
+        t16->rt[threadIdx.x] = rt;
+        t16->ct[threadIdx.x] = ct;
+      }
+    }
   } else {
     const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(S);
     unsigned int m = 0;
@@ -293,7 +374,8 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
 }
 
 // RES_HERM / TILE_HERM: resident / tile items use Hermitian mode (must match
-// BJob::herm as set by batch_herm: FP64 <true, true>, split <true, false>).
+// BJob::herm as set by batch_herm: <true, true> for both precisions; split
+// tile items then walk canonical 16 x 16 tiles).
 template <typename T2, bool RES_HERM, bool TILE_HERM>
 __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const BJob* __restrict__ jobs,
                                                           const BBlk* __restrict__ blks,
@@ -304,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
   T2* sR = sS + kSEntries;
   __shared__ BBlk s_blk;
   __shared__ RowLists s_rl;
+  __shared__ Tile16 s_t16;
   __shared__ int s_idx;
   constexpr bool kF64 = sizeof(T2) == 16;
   for (;;) {
@@ -321,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       const int N = 1 << (2 * n);
       for (int e = threadIdx.x; e < N; e += blockDim.x) sR[e] = Cx<T2>::ldcg(&rho[e]);
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
-        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl);
+        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16);
         const ApplyParams& p = s_blk.p;
         const unsigned long long total = RES_HERM ? p.n_canon : p.n_groups;
         for (unsigned long long g = threadIdx.x; g < total; g += blockDim.x) {
@@ -358,9 +441,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         __nanosleep(128);
       }
     }
-    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl);
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16);
     const ApplyParams& p = s_blk.p;
-    if (*(volatile int*)err == 0) {
+    if (*(volatile int*)err == 0 && !kF64 && TILE_HERM) {
+      // split Hermitian: an item is a range of canonical 16 x 16 tiles
+      const unsigned long long upt = 1ull << tiles16_log2(jb.tile_log2, p.width);
+      const unsigned long long Mt = (1ull << (p.n - p.width)) / 16;
+      const unsigned long long total = Mt * (Mt + 1) / 2;
+      const unsigned long long u0 = (unsigned long long)it.tile0 * upt;
+      const unsigned long long u1 = min(total, u0 + (unsigned long long)it.ntiles * upt);
+      float2* rho32 = reinterpret_cast<float2*>(rho);
+      const float2* s32 = reinterpret_cast<const float2*>(sS);
+      for (unsigned long long u = u0; u < u1; ++u) {
+        if (p.width == 1)
+          apply_tile16<1>(rho32, u, p, s32, s_t16);
+        else
+          apply_tile16<2>(rho32, u, p, s32, s_t16);
+      }
+    } else if (*(volatile int*)err == 0) {
       const unsigned long long gpt = 1ull << (jb.tile_log2 - 2 * p.width);  // groups per tile
       const unsigned long long total = TILE_HERM ? p.n_canon : p.n_groups;
       const unsigned long long g0 = (unsigned long long)it.tile0 * gpt;
@@ -378,9 +476,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
             apply_group_lists_global<2, TILE_HERM>(rho64, g, p, val, s_rl, mine);
         } else {
           if (p.width == 1)
-            apply_group<T2, 1, true, TILE_HERM>(rho, g, p, sS);
+            apply_group<T2, 1, true, false>(rho, g, p, sS);
           else
-            apply_group<T2, 2, true, TILE_HERM>(rho, g, p, sS);
+            apply_group<T2, 2, true, false>(rho, g, p, sS);
         }
       }
     }
@@ -445,28 +543,43 @@ inline bool is_resident(int n, int prec) {
   return (size_t)(prec == 0 ? 16 : 8) << (2 * n) <= (size_t)kResidentBytes;
 }
 
-// Hermitian mode in the batch kernel: every FP64 job (DFMA-bound, so the
-// transposed reads cost little); split jobs only when resident in shared
-// memory (their global passes are HBM-bound and keep full coalesced updates).
-inline bool batch_herm(int n, int prec) { return prec == 0 || is_resident(n, prec); }
+// Hermitian mode in the batch kernel: every job. FP64 and resident split
+// jobs take one canonical group per thread; split tile jobs (at least 7
+// qubits, so 2^(n-w) >= 32 row rests) walk canonical 16 x 16 tiles.
+inline bool batch_herm(int n, int prec) {
+  (void)n;
+  (void)prec;
+  return true;
+}
 
 // Fill the per-block tile counts and wait targets of one job's blocks and
-// return its total tile count. gpt = 2^(tile_log2 - 2w) groups per tile.
-inline long long set_tiles(BBlk* blks, int n_blocks, int tile_log2, bool herm) {
+// return its total tile count. gpt = 2^(tile_log2 - 2w) groups per tile;
+// split tile jobs in Hermitian mode count canonical 16 x 16 tiles instead.
+inline long long set_tiles(BBlk* blks, int n_blocks, int tile_log2, bool herm, bool tiled16) {
   long long prefix = 0;
   for (int b = 0; b < n_blocks; ++b) {
     ApplyParams& p = blks[b].p;
     const unsigned long long M = 1ull << (p.n - p.width);
     p.herm = herm ? 1 : 0;
     p.n_canon = M * (M + 1) / 2;
-    const unsigned long long total = herm ? p.n_canon : p.n_groups;
-    const unsigned long long gpt = 1ull << (tile_log2 - 2 * p.width);
-    blks[b].tiles = (int)((total + gpt - 1) / gpt);
+    unsigned long long total, per;
+    if (herm && tiled16) {
+      const unsigned long long Mt = M / 16;
+      total = Mt * (Mt + 1) / 2;
+      per = 1ull << tiles16_log2(tile_log2, p.width);
+    } else {
+      total = herm ? p.n_canon : p.n_groups;
+      per = 1ull << (tile_log2 - 2 * p.width);
+    }
+    blks[b].tiles = (int)((total + per - 1) / per);
     blks[b].tile_prefix = (int)prefix;
     prefix += blks[b].tiles;
   }
   return prefix;
 }
+
+// Split tile jobs walk canonical 16 x 16 tiles (needs 2^(n-w) >= 16).
+inline bool tiled16_job(int n, int prec) { return prec != 0 && !is_resident(n, prec); }
 
 }  // namespace batch
 }  // namespace tq

@@ -227,8 +227,8 @@ tq_status tq_server_create(int precision, void* cuda_stream, size_t rho_budget_b
       e = cudaFuncSetAttribute(k_batch_apply<double2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<double2, true, true>, kThreads, smem);
     } else {
-      e = cudaFuncSetAttribute(k_batch_apply<float2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2, true, false>, kThreads, smem);
+      e = cudaFuncSetAttribute(k_batch_apply<float2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2, true, true>, kThreads, smem);
     }
   }
   if (e != cudaSuccess) {
@@ -329,7 +329,7 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
       bb.S = sb + (size_t)r.prog.sb_off[b] * esz;
       blks.push_back(bb);
     }
-    set_tiles(blks.data() + j.block0, cnt, j.tile_log2, j.herm != 0);
+    set_tiles(blks.data() + j.block0, cnt, j.tile_log2, j.herm != 0, tiled16_job(r.n, s->prec));
     if (cnt > 0 && j.resident) items.push_back(BItem{(int)jobs.size(), -1, 0, cnt});
     job_req.push_back(id);
     cnts.push_back(cnt);
@@ -372,7 +372,7 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
           static_cast<const BItem*>(s->ditems.ptr), (int)items.size(), static_cast<int*>(s->counters.ptr), ticket,
           ticket + 32, s->max_spin);
     else
-      k_batch_apply<float2, true, false><<<grid, kThreads, apply_smem<float2>(), s->stream>>>(
+      k_batch_apply<float2, true, true><<<grid, kThreads, apply_smem<float2>(), s->stream>>>(
           static_cast<char*>(s->rho_mem.ptr), static_cast<const BJob*>(s->djobs.ptr), static_cast<const BBlk*>(s->dblks.ptr),
           static_cast<const BItem*>(s->ditems.ptr), (int)items.size(), static_cast<int*>(s->counters.ptr), ticket,
           ticket + 32, s->max_spin);

@@ -51,11 +51,11 @@ def test_batch_matches_oracle_and_replays(tq, precision):
 
 def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
     """Flops and HBM bytes tq_batch_work must report for one job, from the
-    plan's block widths: FP64 jobs and resident split jobs run canonical
-    groups; FP64 counts nonzeros (a diagonal block has D of them)."""
+    plan's block widths: every job runs its canonical groups (Hermitian
+    mode); FP64 counts nonzeros (a diagonal block has D of them)."""
     esz = 16 if precision == "fp64" else 8
     resident = esz * 4 ** n <= 64 * 1024
-    herm = precision == "fp64" or resident
+    herm = True
     _, widths = tq.plan_fusion(n, ops, width, precision)
     flops = bytes_ = 0
     for w in widths:
