@@ -68,19 +68,45 @@ def fp64_peak_tflops(sm_mhz: float) -> float:
     return 152 * 4 * sm_mhz * 1e6 / 1e12
 
 
+def kernel_source_sha(symbol: str):
+    """sha256 (first 16 hex digits) of a kernel's definition in csrc/ (from its
+    `__global__` to the closing brace of its body) together with the shared
+    device helpers in tq_device.cuh: changes when the kernel's code does."""
+    csrc = os.path.join(ROOT, "paper_2404_13184_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if not name.endswith((".cu", ".cuh")):
+            continue
+        text = open(os.path.join(csrc, name)).read()
+        at = text.find(" " + symbol + "(")
+        if at < 0:
+            continue
+        start = text.rfind("__global__", 0, at)
+        start = text.rfind("template", 0, start) if text.rfind("template", 0, start) > text.rfind(";", 0, start) else start
+        brace = text.find("{", at)
+        depth, k = 0, brace
+        while k < len(text):
+            depth += {"{": 1, "}": -1}.get(text[k], 0)
+            if depth == 0:
+                break
+            k += 1
+        helpers = open(os.path.join(csrc, "tq_device.cuh")).read()
+        return hashlib.sha256((text[start:k + 1] + helpers).encode()).hexdigest()[:16]
+    return None
+
+
 def traffic_from_profile(kernel: str):
     """dram read+write bytes per launch from the committed ncu summary of
-    `kernel`, if the kernel source is unchanged since the capture."""
+    `kernel`, if the kernel's source is unchanged since the capture (the
+    summary names the kernel's symbol and the hash kernel_source_sha gave)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}.txt")
-    src = os.path.join(ROOT, "paper_2404_13184_gb300", "csrc", "tq_apply.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = {}
         for line in open(path):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
-                fields[k.strip()] = v.strip()
-        if fields.get("source_sha256_16") != sha:
+                fields[k.strip()] = v.split("#")[0].strip()
+        sym = fields.get("kernel_symbol")
+        if not sym or fields.get("source_sha256_16") != kernel_source_sha(sym):
             return None
         return float(fields["dram_bytes_per_full_launch"])
     except Exception:

@@ -226,12 +226,11 @@ cudaError_t run_sparse(double2* rho, const SparseBlock* sp, const ApplyParams& p
 // Hermitian mode for split states (widths 1, 2). The pass is HBM-bound, so
 // the canonical groups are walked in T x T tiles: row-rest a in
 // [ta T, ta T + T), column-rest b in [tb T, tb T + T), ta <= tb, one thread
-// per group with consecutive threads along a. Entries on or above the
-// diagonal are read and written in place (coalesced along a); entries below
-// it are held by their transposes, whose rows follow a, so a warp touches 16
-// rows there, and the neighbouring warps of the same tile use the rest of
-// each 32-byte sector while it is still in L1. Diagonal tiles (ta == tb)
-// compute the groups with a <= b.
+// per group; a warp covers 8 consecutive a by 4 consecutive b. Entries on or
+// above the diagonal are read and written in place (8 consecutive rows of a
+// column); entries below it are held by their transposes, whose 4
+// consecutive columns of a row fill one 32-byte sector. Diagonal tiles
+// (ta == tb) compute the groups with a <= b.
 //
 // Row index r = dep(a) + rt[l], column index c = dep(b) + ct[l], vec index
 // r + c 2^n; dep() inserts zeros at the target qubits (the same positions for
@@ -271,7 +270,12 @@ __global__ void __launch_bounds__(T * T) k_apply_herm_tiled(float2* rho, const f
   __syncthreads();
   const unsigned int* rt = s_rt;  // warp-uniform reads (broadcast)
   const unsigned int* ct = s_ct;
-  const int i = threadIdx.x % T, j = threadIdx.x / T;
+  // a warp covers 8 row rests x 4 column rests: 8 consecutive rows of one
+  // column above the diagonal (64 B), 4 consecutive columns of one row
+  // below it (one full 32-byte sector)
+  static_assert(T == 16, "warp layout of a 16 x 16 tile");
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int i = (lane % 8) + 8 * (w % 2), j = (lane / 8) + 4 * (w / 2);
   const unsigned int di = s_dep[i], dj = s_dep[j];
   const unsigned long long Mt = (1ull << (p.n - K)) / T;
   const unsigned long long n_tiles = Mt * (Mt + 1) / 2;

@@ -155,10 +155,9 @@ static_assert(16 * kThreads * 16 <= kResidentBytes, "operand columns of a width-
 // tiles of (row rest a, column rest b), one group per thread: thread (i, j)
 // takes a = 16 ta + i, b = 16 tb + j. Rows are dep(16 ta) + dep16[i] + rt[l]
 // (dep inserts zeros at the target qubits and is additive over disjoint
-// bits), columns likewise; consecutive threads take consecutive rows, so
-// entries above the diagonal are read and written coalesced, and the
-// transposed entries below it share 32-byte sectors with the neighbouring
-// warps of the same tile.
+// bits), columns likewise; a warp covers 8 consecutive a by 4 consecutive
+// b, so entries above the diagonal are read and written 8 rows at a time
+// and transposed entries below it 4 columns (one 32-byte sector) at a time.
 struct Tile16 {
   unsigned dep16[16];
   unsigned rt[16], ct[16];  // row / column target bits of local index l
@@ -281,7 +280,10 @@ template <int K>
 __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, const ApplyParams& p,
                                              const float2* sS, const Tile16& t) {
   constexpr int D = 1 << (2 * K);
-  const int i = threadIdx.x % 16, j = threadIdx.x / 16;
+  // a warp covers 8 row rests x 4 column rests (full 32-byte sectors in both
+  // orientations)
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int i = (lane % 8) + 8 * (w % 2), j = (lane / 8) + 4 * (w / 2);
   bool diag = false;
   const unsigned long long tt = canonical_group(u, 32, &diag);  // (ta, tb) as ta | tb << 32
   if (diag && i > j) return;  // not a canonical group
