@@ -358,8 +358,11 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
     circuits (n ~ U{5..15}, depth ~ U{50..2000}, 30% CX, depolarising and
     amplitude damping per request) served by the continuous-batching loop.
     The FIFO queue is kept in arrival order; a request is materialised and
-    handed to the server when it reaches the head (a lookahead of 8), and its
-    latency is measured from its arrival time. Requests unfinished when the
+    handed to the server when it reaches the head (a lookahead of 8; at most
+    one per tick), and its latency is measured from its arrival time to the
+    tick that collects its result. Ticks are pipelined (tq_server_step_async):
+    the client's work overlaps the GPU, and gpu_busy_frac is the GPU time of
+    the ticks (CUDA events) over the wall time. Requests unfinished when the
     drain window ends are censored."""
     import numpy as np
     from paper_2404_13184_gb300 import workloads
@@ -371,12 +374,13 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
     inflight = {}            # rid -> (arrival time, n, depth)
     lat, done_n = [], []
     queued_in_server = 0
-    busy = 0.0
     while True:
         now = time.perf_counter() - t0
         if now > duration + drain:
             break
-        while nxt < len(arrivals) and arrivals[nxt] <= now and queued_in_server < 8:
+        # at most one submission per tick, so planning a request overlaps the
+        # tick running on the GPU
+        if nxt < len(arrivals) and arrivals[nxt] <= now and queued_in_server < 8:
             c = workloads.served_request(rng)
             rid = srv.submit(c.n, c.ops, width=2, masks=[1])
             inflight[rid] = (arrivals[nxt], c.n, c.n_gates)
@@ -387,9 +391,9 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
                 break
             time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
             continue
-        ts = time.perf_counter()
-        live, queued_in_server, fin = srv.step()
-        busy += time.perf_counter() - ts
+        # pipelined ticks: this call collects the previous tick and launches
+        # the next, so building and submitting requests overlaps the GPU
+        live, queued_in_server, fin = srv.step_async()
         if fin:
             tdone = time.perf_counter() - t0
             for rid in list(inflight):
@@ -402,6 +406,7 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
     end = wall
     censored = [end - a for a, _, _ in inflight.values()] + [end - a for a in arrivals[nxt:] if a <= end]
     info = srv.info()
+    busy = srv.gpu_ms() / 1e3      # GPU time of the collected ticks (CUDA events)
     srv.free()
     lat_sorted = sorted(lat)
 

@@ -348,6 +348,20 @@ tq_status tq_server_submit(tq_server* s, int n_qubits, const tq_op* ops, size_t 
  * requests, requests finished in this tick. */
 tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finished);
 
+/* Pipelined tick: first collect the tick launched by the previous call
+ * (waits for it; *n_finished = requests it finished, whose results
+ * tq_server_poll now returns), then admit and launch the next tick and
+ * return without waiting, so the caller's own work (building and
+ * submitting requests, polling) overlaps the GPU. *n_live and *n_queued
+ * describe the state after the launched tick. Bounded-wait timeouts of a
+ * tick are reported by the call that collects it. Mixing with
+ * tq_server_step is allowed: tq_server_step collects a pending tick first. */
+tq_status tq_server_step_async(tq_server* s, int* n_live, int* n_queued, int* n_finished);
+
+/* GPU time of all collected ticks (CUDA events around each tick's
+ * admission, apply and readout work), in milliseconds. */
+tq_status tq_server_gpu_ms(const tq_server* s, double* ms);
+
 /* *state: 0 queued, 1 live, 2 done; when done, out (if not NULL) receives
  * 2 + n_masks doubles as in tq_batch_result. */
 tq_status tq_server_poll(tq_server* s, int request_id, int* state, double* out);

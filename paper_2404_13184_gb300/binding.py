@@ -92,6 +92,8 @@ _SIGNATURES = [
     ("tq_server_submit", c_int, [c_void_p, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_uint64), c_int,
                                  POINTER(c_int)]),
     ("tq_server_step", c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    ("tq_server_step_async", c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    ("tq_server_gpu_ms", c_int, [c_void_p, POINTER(c_double)]),
     ("tq_server_poll", c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
     ("tq_server_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(ctypes.c_ulonglong),
                                POINTER(ctypes.c_ulonglong)]),
@@ -307,6 +309,19 @@ class Server:
         a, b, c = c_int(0), c_int(0), c_int(0)
         _check(_lib.tq_server_step(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tq_server_step")
         return a.value, b.value, c.value
+
+    def step_async(self):
+        """Collect the previous tick, launch the next one, return at once:
+        (live after the launched tick, queued, finished by the collected tick)."""
+        a, b, c = c_int(0), c_int(0), c_int(0)
+        _check(_lib.tq_server_step_async(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "tq_server_step_async")
+        return a.value, b.value, c.value
+
+    def gpu_ms(self) -> float:
+        v = c_double(0.0)
+        _check(_lib.tq_server_gpu_ms(self._h, ctypes.byref(v)), "tq_server_gpu_ms")
+        return v.value
 
     def poll(self, rid: int):
         st = c_int(0)

@@ -117,14 +117,20 @@ int rest_of(int i, const int* pos, int k, int W) {
 
 // Pattern p (width k) placed at block positions pos[0..k-1] of a width-W block.
 Pattern embed(const Pattern& p, const int* pos, int W) {
+  bool identity = p.width == W;
+  for (int j = 0; j < p.width && identity; ++j) identity = pos[j] == j;
+  if (identity) return p;
   Pattern o;
   o.width = W;
   const int D = 1 << (2 * W);
+  int rest[16], idx[16];
+  for (int i = 0; i < D; ++i) {
+    rest[i] = rest_of(i, pos, p.width, W);
+    idx[i] = op_index(i, pos, p.width, W);
+  }
   for (int i = 0; i < D; ++i)
     for (int j = 0; j < D; ++j)
-      if (rest_of(i, pos, p.width, W) == rest_of(j, pos, p.width, W) &&
-          ((p.row[op_index(i, pos, p.width, W)] >> op_index(j, pos, p.width, W)) & 1))
-        o.row[i] |= (uint16_t)(1u << j);
+      if (rest[i] == rest[j] && ((p.row[idx[i]] >> idx[j]) & 1)) o.row[i] |= (uint16_t)(1u << j);
   return o;
 }
 

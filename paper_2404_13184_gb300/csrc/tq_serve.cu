@@ -99,6 +99,14 @@ struct tq_server {
   int next_id = 0;
   size_t rho_live_bytes = 0;
   unsigned long long ticks = 0, blocks_applied = 0;
+  // the launched, not yet collected tick: requests it finishes (results land
+  // in `pin` at res_off), whether it ran items (error flag at err_off)
+  bool pending = false;
+  std::vector<int> pend_done;
+  bool pend_items = false;
+  size_t res_off = 0, err_off = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // GPU time of the pending tick
+  double gpu_ms = 0.0;
 };
 
 namespace {
@@ -231,6 +239,8 @@ tq_status tq_server_create(int precision, void* cuda_stream, size_t rho_budget_b
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2, true, true>, kThreads, smem);
     }
   }
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev1);
   if (e != cudaSuccess) {
     tq_server_free(s);
     return st_of(e);
@@ -266,11 +276,46 @@ tq_status tq_server_submit(tq_server* s, int n_qubits, const tq_op* ops, size_t 
   return TQ_OK;
 }
 
-tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finished) {
-  if (!s) return TQ_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// Collect the pending tick: wait for it, hand the finished requests their
+// readouts and release their memory. *n_finished: requests it finished.
+tq_status collect_tick(tq_server* s, int* n_finished) {
   if (n_finished) *n_finished = 0;
+  if (!s->pending) return TQ_OK;
+  s->pending = false;
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return st_of(e);
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, s->ev0, s->ev1) == cudaSuccess) s->gpu_ms += ms;
+  const char* h = static_cast<const char*>(s->pin.ptr);
+  int err_flag = 0;
+  if (s->pend_items) std::memcpy(&err_flag, h + s->err_off, sizeof(int));
+  if (!s->pend_done.empty()) {
+    const double* res = reinterpret_cast<const double*>(h + s->res_off);
+    for (size_t k = 0; k < s->pend_done.size(); ++k) {
+      Req& r = s->reqs[s->pend_done[k]];
+      std::memcpy(r.result, res + k * kResults, kResults * sizeof(double));
+      retire(s, r);
+    }
+    std::vector<int> still;
+    for (int id : s->live)
+      if (s->reqs[id].state == 1) still.push_back(id);
+    s->live.swap(still);
+  }
+  if (n_finished) *n_finished = (int)s->pend_done.size();
+  s->pend_done.clear();
+  return err_flag ? TQ_ERR_TIMEOUT : TQ_OK;
+}
+
+// Admit and launch one tick without waiting for it (the previous tick must
+// have been collected).
+tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
   cudaError_t e0 = cudaStreamSynchronize(s->stream);  // the staging buffer is reused below
   if (e0 != cudaSuccess) return st_of(e0);
+  cudaEventRecord(s->ev0, s->stream);
   // 1. admission, FIFO by HBM footprint: stop at the first request that does not fit
   size_t stage_need = 0;
   std::vector<int> admit_ids;
@@ -379,7 +424,8 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
     e = cudaGetLastError();
     if (e != cudaSuccess) return st_of(e);
   }
-  // 3. progress, and readouts of the requests that finished this tick
+  // 3. progress; readouts of the requests this tick finishes are reduced and
+  // copied to the staging buffer behind the tick (collected later)
   std::vector<BJob> done_jobs;
   std::vector<int> done_ids;
   for (size_t j = 0; j < jobs.size(); ++j) {
@@ -391,15 +437,17 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
       done_ids.push_back(job_req[j]);
     }
   }
-  int err_flag = 0;
+  const size_t bj = done_jobs.size() * sizeof(BJob);
+  const size_t br = done_jobs.size() * kResults * sizeof(double);
+  e = cudaStreamSynchronize(s->stream);  // staging reuse
+  if (e == cudaSuccess) e = grow_pin(s->pin, align_up(bj, 256) + br + 256);
+  if (e != cudaSuccess) return st_of(e);
+  char* h = static_cast<char*>(s->pin.ptr);
+  s->res_off = align_up(bj, 256);
+  s->err_off = s->res_off + br;
   if (!done_jobs.empty()) {
-    const size_t bj = done_jobs.size() * sizeof(BJob);
-    const size_t br = done_jobs.size() * kResults * sizeof(double);
     e = grow_dev(s->results, br + bj);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // staging reuse
-    if (e == cudaSuccess) e = grow_pin(s->pin, bj + br + 256);
     if (e != cudaSuccess) return st_of(e);
-    char* h = static_cast<char*>(s->pin.ptr);
     std::memcpy(h, done_jobs.data(), bj);
     char* dres = static_cast<char*>(s->results.ptr);
     e = cudaMemcpyAsync(dres + br, h, bj, cudaMemcpyHostToDevice, s->stream);
@@ -414,36 +462,49 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
             reinterpret_cast<double*>(dres));
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h + align_up(bj, 256), dres, br, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess && !items.empty())
-      e = cudaMemcpyAsync(h + align_up(bj, 256) + br, static_cast<int*>(s->ctl.ptr) + 32, sizeof(int),
-                          cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h + s->res_off, dres, br, cudaMemcpyDeviceToHost, s->stream);
     if (e != cudaSuccess) return st_of(e);
-    const double* res = reinterpret_cast<const double*>(h + align_up(bj, 256));
-    if (!items.empty()) std::memcpy(&err_flag, h + align_up(bj, 256) + br, sizeof(int));
-    for (size_t k = 0; k < done_ids.size(); ++k) {
-      Req& r = s->reqs[done_ids[k]];
-      std::memcpy(r.result, res + k * kResults, kResults * sizeof(double));
-      retire(s, r);
-    }
-    std::vector<int> still;
-    for (int id : s->live)
-      if (s->reqs[id].state == 1) still.push_back(id);
-    s->live.swap(still);
-  } else {
-    if (!items.empty()) {
-      e = cudaMemcpyAsync(&err_flag, static_cast<int*>(s->ctl.ptr) + 32, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-      if (e != cudaSuccess) return st_of(e);
-    }
   }
+  if (!items.empty()) {
+    e = cudaMemcpyAsync(h + s->err_off, static_cast<int*>(s->ctl.ptr) + 32, sizeof(int), cudaMemcpyDeviceToHost,
+                        s->stream);
+    if (e != cudaSuccess) return st_of(e);
+  }
+  cudaEventRecord(s->ev1, s->stream);
+  s->pending = true;
+  s->pend_done.swap(done_ids);
+  s->pend_items = !items.empty();
   ++s->ticks;
-  if (n_live) *n_live = (int)s->live.size();
+  if (n_live) *n_live = (int)(s->live.size() - s->pend_done.size());
   if (n_queued) *n_queued = (int)s->queue.size();
-  if (n_finished) *n_finished = (int)done_ids.size();
   (void)admitted;
-  return err_flag ? TQ_ERR_TIMEOUT : TQ_OK;
+  return TQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finished) {
+  if (!s) return TQ_ERR_ARG;
+  if (n_finished) *n_finished = 0;
+  tq_status st = collect_tick(s, nullptr);  // a tick launched by tq_server_step_async
+  if (st != TQ_OK) return st;
+  if ((st = launch_tick(s, n_live, n_queued)) != TQ_OK) return st;
+  return collect_tick(s, n_finished);
+}
+
+tq_status tq_server_step_async(tq_server* s, int* n_live, int* n_queued, int* n_finished) {
+  if (!s) return TQ_ERR_ARG;
+  tq_status st = collect_tick(s, n_finished);
+  if (st != TQ_OK) return st;
+  return launch_tick(s, n_live, n_queued);
+}
+
+tq_status tq_server_gpu_ms(const tq_server* s, double* ms) {
+  if (!s || !ms) return TQ_ERR_ARG;
+  *ms = s->gpu_ms;
+  return TQ_OK;
 }
 
 tq_status tq_server_poll(tq_server* s, int request_id, int* state, double* out) {
@@ -471,6 +532,8 @@ void tq_server_free(tq_server* s) {
   for (DevBuf* d : {&s->rho_mem, &s->tab_mem, &s->djobs, &s->dblks, &s->ditems, &s->counters, &s->ctl, &s->results})
     if (d->ptr) cudaFree(d->ptr);
   if (s->pin.ptr) cudaFreeHost(s->pin.ptr);
+  for (cudaEvent_t ev : {s->ev0, s->ev1})
+    if (ev) cudaEventDestroy(ev);
   delete s;
 }
 

@@ -171,19 +171,27 @@ def served_request(rng: np.random.Generator, n_min: int = 5, n_max: int = 15, d_
     depth = int(rng.integers(d_min, d_max + 1))
     p = float(10 ** rng.uniform(-4, -2))
     gamma = float(10 ** rng.uniform(-5, -3))
+    # per-gate draws in bulk: gate kind, qubits (a CX pair uniform over
+    # ordered pairs of distinct qubits), 1-qubit gate and angle
+    two = (rng.uniform(size=depth) < frac_2q).tolist()
+    qa = rng.integers(n, size=depth).tolist()
+    qb = rng.integers(max(1, n - 1), size=depth).tolist()
+    g1 = rng.integers(3, size=depth).tolist()
+    ang = rng.uniform(0, 2 * math.pi, size=depth).tolist()
     ops = []
-    for _ in range(depth):
-        if rng.uniform() < frac_2q:
-            q = [int(v) for v in rng.choice(n, size=2, replace=False)]
+    for t in range(depth):
+        a = qa[t]
+        if two[t]:
+            b = qb[t] + (qb[t] >= a)
+            q = [a, b]
             ops.append(("cx", q, ()))
             ops.append(("depol", q, (p,)))
-            ops.append(("ad", [q[0]], (gamma,)))
-            ops.append(("ad", [q[1]], (gamma,)))
+            ops.append(("ad", [a], (gamma,)))
+            ops.append(("ad", [b], (gamma,)))
         else:
-            g = ("h", "rx", "rz")[int(rng.integers(3))]
-            q = [int(rng.integers(n))]
-            params = () if g == "h" else (float(rng.uniform(0, 2 * math.pi)),)
-            ops.append((g, q, params))
+            g = ("h", "rx", "rz")[g1[t]]
+            q = [a]
+            ops.append((g, q, () if g == "h" else (ang[t],)))
             ops.append(("depol", q, (p,)))
             ops.append(("ad", q, (gamma,)))
     return Circuit(n=n, ops=ops, n_gates=depth, label=f"req-{n}q-{depth}g")

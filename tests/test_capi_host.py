@@ -253,3 +253,13 @@ def test_sparsity_aware_planning():
     assert B.op_pattern(("depol", [0, 1], (0.1,))).sum() == 28      # 12 coherences + 4 x 4 populations
     assert B.op_pattern(("depol", [0], (0.1,))).sum() == 6
     assert B.op_pattern(("cx", [0, 1], ())).sum() == 16             # a permutation
+
+
+def test_register_size_limits_are_checked_before_any_gpu_work(lib):
+    # n in [1, 16]: outside it tq_create / tq_batch_add fail with TQ_ERR_ARG
+    # and touch no device (this runs on machines without a GPU)
+    h = B.ctypes.c_void_p()
+    for n in (0, 17, -1):
+        assert lib.tq_create(n, 0, None, B.ctypes.byref(h)) == 1
+        assert not h.value
+    assert lib.tq_create(3, 7, None, B.ctypes.byref(h)) == 1          # unknown precision

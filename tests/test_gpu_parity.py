@@ -267,6 +267,15 @@ def test_full_size_15q_factorised_split(tq):
     _factorised_check(tq, 15, [1, 7, 12, 14], -1, "split", 30, 16, tol=2e-6)
 
 
+def test_max_size_16q_factorised_fp64(tq):
+    # the largest register (vec(rho) = 64 GiB in FP64; vec indices up to 2^32 - 1)
+    _factorised_check(tq, 16, [0, 7, 14, 15], -1, "fp64", 10, 17)
+
+
+def test_max_size_16q_factorised_split(tq):
+    _factorised_check(tq, 16, [2, 8, 13, 15], -1, "split", 20, 18, tol=2e-6)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_device_program_equals_host_call(tq, precision):
     import torch

@@ -68,6 +68,40 @@ def test_served_results_same_alone_and_in_mix(tq, precision):
     srv.free()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_pipelined_ticks_give_the_same_results(tq, precision):
+    # tq_server_step_async collects the previous tick and launches the next
+    # without waiting; every request's result equals the synchronous run's
+    reqs = _requests(12, 7)
+    runs = []
+    for mode in ("sync", "async"):
+        srv = tq.Server(precision, rho_budget=64 << 20, max_live=5)
+        ids = [srv.submit(n, ops, width=2, masks=masks) for n, ops, masks in reqs[:6]]
+        pending = list(reqs[6:])
+        done, ticks = {}, 0
+        while len(done) < len(reqs) and ticks < 10000:
+            if pending:
+                n, ops, masks = pending.pop(0)
+                ids.append(srv.submit(n, ops, width=2, masks=masks))
+            live, queued, fin = srv.step() if mode == "sync" else srv.step_async()
+            assert live <= 5
+            ticks += 1
+            for k, rid in enumerate(ids):
+                if k not in done:
+                    st, res = srv.poll(rid)
+                    if st == 2:
+                        done[k] = res
+        assert len(done) == len(reqs)
+        assert srv.info()["rho_live_bytes"] == 0 and srv.gpu_ms() > 0
+        runs.append(done)
+        srv.free()
+    for k in range(len(reqs)):
+        if precision == "fp64":
+            assert np.array_equal(runs[0][k], runs[1][k]), k
+        else:
+            assert np.max(np.abs(runs[0][k] - runs[1][k])) < 1e-6, k
+
+
 def test_admission_respects_the_hbm_budget(tq):
     # room for exactly two 8-qubit FP64 density matrices (1 MiB each): at most
     # two requests can be admitted (and so finish) per tick
