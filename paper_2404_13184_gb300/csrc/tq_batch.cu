@@ -188,6 +188,7 @@ tq_status finalize(tq_batch* b) {
 
   tq_program P;  // layout of the concatenated upload
   P.n_ops = all.ops.size();
+  P.n_uops = all.ops.size();
   size_t off = 0;
   P.o_kraus = off; off = align_up(off + all.kraus.size() * sizeof(double2), 256);
   P.o_ops = off;   off = align_up(off + all.ops.size() * sizeof(OpDesc), 256);
@@ -255,9 +256,9 @@ tq_status finalize(tq_batch* b) {
   cudaMemsetAsync(b->arena.ptr, 0, arena, st);
   k_batch_set_one<<<(n_jobs + 255) / 256, 256, 0, st>>>(static_cast<char*>(b->arena.ptr),
                                                         static_cast<const BJob*>(b->djobs.ptr), n_jobs, b->prec);
-  if (P.n_ops > 0) {
+  if (P.n_uops > 0) {
     launch_build_superops(reinterpret_cast<const double2*>(d + P.o_kraus), reinterpret_cast<const OpDesc*>(d + P.o_ops),
-                          (int)P.n_ops, max_dim2, static_cast<double2*>(b->sops.ptr), st);
+                          (int)P.n_uops, max_dim2, static_cast<double2*>(b->sops.ptr), st);
     launch_fuse(static_cast<const double2*>(b->sops.ptr), reinterpret_cast<const OpDesc*>(d + P.o_ops),
                 reinterpret_cast<const BlockDesc*>(d + P.o_blk), reinterpret_cast<const MemberDesc*>(d + P.o_mem),
                 reinterpret_cast<const FuseWork*>(d + P.o_work), (int)all.work.size(),

@@ -2,6 +2,8 @@
 // (Kraus sets, TANQ-Sim Sec. 3.5), op validation, the fusion planner
 // (Sec. 3.3) and small helpers. No GPU work happens in this file.
 #include <algorithm>
+#include <map>
+#include <array>
 #include <cmath>
 #include <cstring>
 
@@ -478,13 +480,25 @@ tq_status tq_plan_fusion(int n, const tq_op* ops, size_t n_ops, int max_width, i
   if (n < 1 || n > kMaxQubits || (!ops && n_ops) || !n_blocks_out) return TQ_ERR_ARG;
   if (precision != TQ_FP64 && precision != TQ_SPLIT) return TQ_ERR_ARG;
   std::vector<PlanOp> pops(n_ops);
+  // named gates and channels with equal parameters share one pattern
+  std::map<std::array<uint64_t, 7>, size_t> seen;
   for (size_t i = 0; i < n_ops; ++i) {
     tq_status st = validate_op(n, ops[i]);
     if (st != TQ_OK) return st;
+    pops[i].qubits.assign(ops[i].qubits, ops[i].qubits + ops[i].k);
+    const bool named = ops[i].kind == TQ_OP_GATE || ops[i].kind == TQ_OP_CHANNEL;
+    std::array<uint64_t, 7> key{(uint64_t)ops[i].kind, (uint64_t)ops[i].name, (uint64_t)ops[i].k, 0, 0, 0, 0};
+    std::memcpy(&key[3], ops[i].params, 4 * sizeof(double));
+    auto it = named ? seen.find(key) : seen.end();
+    if (it != seen.end()) {
+      pops[i].has_pat = pops[it->second].has_pat;
+      pops[i].pat = pops[it->second].pat;
+      continue;
+    }
     ResolvedOp r;
     if ((st = resolve_op(ops[i], &r)) != TQ_OK) return st;
-    pops[i].qubits.assign(ops[i].qubits, ops[i].qubits + ops[i].k);
     pops[i].has_pat = op_pattern(ops[i], r, &pops[i].pat);
+    if (named) seen.emplace(key, i);
   }
   std::vector<Block> blocks;
   tq_status st = plan_fusion(n, pops, max_width, precision, &blocks);

@@ -41,7 +41,8 @@ struct HostTables {
 struct tq_program {
   int n = 0;
   int prec = 0;
-  size_t n_ops = 0;
+  size_t n_ops = 0;   // ops of the circuit
+  size_t n_uops = 0;  // distinct op descriptors (superoperators built): identical named ops share one
   int max_width = 0;
   int max_dim2 = 0;
   int n_work = 0;

@@ -175,9 +175,9 @@ tq_status admit(tq_server* s, Req& r, char* stage, size_t* stage_used) {
   pack_blob(P, r.t, h);
   *stage_used = align_up(*stage_used + P.blob_bytes, 256);
   cudaError_t e = cudaMemcpyAsync(tab, h, P.blob_bytes, cudaMemcpyHostToDevice, s->stream);
-  if (e == cudaSuccess && P.n_ops > 0) {
+  if (e == cudaSuccess && P.n_uops > 0) {
     e = launch_build_superops(reinterpret_cast<const double2*>(tab + P.o_kraus), reinterpret_cast<const OpDesc*>(tab + P.o_ops),
-                              (int)P.n_ops, P.max_dim2, reinterpret_cast<double2*>(tab + r.o_sops), s->stream);
+                              (int)P.n_uops, P.max_dim2, reinterpret_cast<double2*>(tab + r.o_sops), s->stream);
     if (e == cudaSuccess)
       e = launch_fuse(reinterpret_cast<const double2*>(tab + r.o_sops), reinterpret_cast<const OpDesc*>(tab + P.o_ops),
                       reinterpret_cast<const BlockDesc*>(tab + P.o_blk), reinterpret_cast<const MemberDesc*>(tab + P.o_mem),

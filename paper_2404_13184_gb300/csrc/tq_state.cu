@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "tq_device.cuh"
@@ -199,28 +200,64 @@ ApplyParams apply_params(int n, const Block& B) {
 }
 
 // Validate, resolve and plan `ops` into P's host fields and `t`.
+// Identity of a named gate or channel: its superoperator depends on nothing
+// else (not on the qubits it acts on).
+struct OpKey {
+  int kind, name, k;
+  uint64_t p[4];
+  bool operator==(const OpKey& o) const {
+    return kind == o.kind && name == o.name && k == o.k && p[0] == o.p[0] && p[1] == o.p[1] && p[2] == o.p[2] &&
+           p[3] == o.p[3];
+  }
+};
+struct OpKeyHash {
+  size_t operator()(const OpKey& key) const {
+    uint64_t h = (uint64_t)key.kind * 0x9E3779B97F4A7C15ull ^ (uint64_t)key.name * 0xC2B2AE3D27D4EB4Full ^ (uint64_t)key.k;
+    for (uint64_t v : key.p) h = (h ^ v) * 0x100000001B3ull;
+    return (size_t)h;
+  }
+};
+
 tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t) {
   if (width < -1 || width > kMaxWidth) return TQ_ERR_ARG;
   std::vector<PlanOp> qs(n_ops);
-  t->ops.resize(n_ops);
+  std::vector<int> uop(n_ops);  // op -> its descriptor (identical named ops share one)
+  std::vector<Pattern> upat;
+  std::vector<char> uhas;
+  std::unordered_map<OpKey, int, OpKeyHash> seen;
+  t->ops.clear();
   P->max_dim2 = 0;
   for (size_t i = 0; i < n_ops; ++i) {
     tq_status st = validate_op(n, ops[i]);
     if (st != TQ_OK) return st;
-    ResolvedOp r;
-    st = resolve_op(ops[i], &r);
-    if (st != TQ_OK) return st;
+    const bool named = ops[i].kind == TQ_OP_GATE || ops[i].kind == TQ_OP_CHANNEL;
+    OpKey key{ops[i].kind, ops[i].name, ops[i].k, {0, 0, 0, 0}};
+    std::memcpy(key.p, ops[i].params, sizeof(key.p));
+    auto it = named ? seen.find(key) : seen.end();
+    if (it != seen.end()) {
+      uop[i] = it->second;
+    } else {
+      ResolvedOp r;
+      st = resolve_op(ops[i], &r);
+      if (st != TQ_OK) return st;
+      uop[i] = (int)t->ops.size();
+      upat.emplace_back();
+      uhas.push_back(op_pattern(ops[i], r, &upat.back()) ? 1 : 0);
+      OpDesc od{};
+      od.k = r.k;
+      od.m = r.m;
+      od.kraus_off = (long long)t->kraus.size();
+      od.sop_off = t->sop_entries;
+      for (const cplx& v : r.kraus) t->kraus.push_back(make_double2(v.real(), v.imag()));
+      const long long d2 = 1ll << (2 * r.k);
+      t->sop_entries += d2 * d2;
+      P->max_dim2 = std::max<int>(P->max_dim2, (int)(d2 * d2));
+      t->ops.push_back(od);
+      if (named) seen.emplace(key, uop[i]);
+    }
     qs[i].qubits.assign(ops[i].qubits, ops[i].qubits + ops[i].k);
-    qs[i].has_pat = op_pattern(ops[i], r, &qs[i].pat);
-    OpDesc& od = t->ops[i];
-    od.k = r.k;
-    od.m = r.m;
-    od.kraus_off = (long long)t->kraus.size();
-    od.sop_off = t->sop_entries;
-    for (const cplx& v : r.kraus) t->kraus.push_back(make_double2(v.real(), v.imag()));
-    const long long d2 = 1ll << (2 * r.k);
-    t->sop_entries += d2 * d2;
-    P->max_dim2 = std::max<int>(P->max_dim2, (int)(d2 * d2));
+    qs[i].has_pat = uhas[uop[i]] != 0;
+    qs[i].pat = upat[uop[i]];
   }
   std::vector<Block> plan;
   tq_status st = plan_fusion(n, qs, width, prec, &plan);
@@ -228,6 +265,7 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
   P->n = n;
   P->prec = prec;
   P->n_ops = n_ops;
+  P->n_uops = t->ops.size();
   P->max_width = 0;
   P->params.clear();
   P->sb_off.clear();
@@ -245,7 +283,7 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
     t->sb_entries += (long long)D * D;
     for (int oi : B.ops) {
       MemberDesc md{};
-      md.op = oi;
+      md.op = uop[oi];
       md.k = ops[oi].k;
       for (int j = 0; j < md.k; ++j)
         md.pos[j] = (int)(std::find(B.qubits, B.qubits + B.width, ops[oi].qubits[j]) - B.qubits);
@@ -294,7 +332,7 @@ namespace {
 
 // Enqueue superoperator build, fusion and every apply pass of P on s.
 tq_status enqueue_program(tq_state* s, const tq_program& P) {
-  if (P.n_ops == 0) return TQ_OK;
+  if (P.n_uops == 0) return TQ_OK;
   char* d = static_cast<char*>(P.blob.ptr);
   const double2* d_kraus = reinterpret_cast<const double2*>(d + P.o_kraus);
   const OpDesc* d_ops = reinterpret_cast<const OpDesc*>(d + P.o_ops);
@@ -304,8 +342,8 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
   double2* sops = static_cast<double2*>(P.sops.ptr);
   double2* sb64 = static_cast<double2*>(P.sb64.ptr);
   float2* sb32 = P.prec == TQ_SPLIT ? static_cast<float2*>(P.sb32.ptr) : nullptr;
-  cudaError_t e = timed(s, K_BUILD, build_superops_launches((int)P.n_ops), [&] {
-    return launch_build_superops(d_kraus, d_ops, (int)P.n_ops, P.max_dim2, sops, s->stream);
+  cudaError_t e = timed(s, K_BUILD, build_superops_launches((int)P.n_uops), [&] {
+    return launch_build_superops(d_kraus, d_ops, (int)P.n_uops, P.max_dim2, sops, s->stream);
   });
   if (e == cudaSuccess)
     e = timed(s, K_FUSE, 1, [&] { return launch_fuse(sops, d_ops, d_blk, d_mem, d_work, P.n_work, sb64, sb32, s->stream); });
@@ -414,6 +452,7 @@ tq_status run_impl(tq_state* s, const tq_op* ops, size_t n_ops, int width, size_
   P.n = plan.n;
   P.prec = plan.prec;
   P.n_ops = plan.n_ops;
+  P.n_uops = plan.n_uops;
   P.max_width = plan.max_width;
   P.max_dim2 = plan.max_dim2;
   P.n_work = plan.n_work;
