@@ -321,7 +321,9 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
 // placing row i after the counts of rows < i.
 template <typename T2>
 __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl, Tile16* t16) {
-  if (threadIdx.x == 0) *s_blk = *blk;
+  static_assert(sizeof(BBlk) % 8 == 0 && sizeof(BBlk) / 8 <= kThreads, "descriptor copied one word per thread");
+  if (threadIdx.x < sizeof(BBlk) / 8)  // in parallel: one 8-byte word per thread
+    reinterpret_cast<unsigned long long*>(s_blk)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(blk)[threadIdx.x];
   __syncthreads();
   const int D = 1 << (2 * s_blk->p.width);
   const T2* S = static_cast<const T2*>(s_blk->S);
@@ -430,9 +432,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       __syncthreads();
       continue;
     }
-    // tile item: wait until every tile of the previous block of this job is done
+    // tile item: stage the block (independent of earlier blocks), then wait
+    // until every tile of the previous block of this job is done
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16);
     if (threadIdx.x == 0 && it.block > 0) {
-      const int need = jb.never_ready ? 0x7fffffff : blks[jb.block0 + it.block].tile_prefix;
+      const int need = jb.never_ready ? 0x7fffffff : s_blk.tile_prefix;
       long long spins = 0;
       while (ld_acquire(&counters[it.job]) < need) {
         if (ld_acquire(err) != 0) break;
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         __nanosleep(128);
       }
     }
-    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16);
+    __syncthreads();
     const ApplyParams& p = s_blk.p;
     if (*(volatile int*)err == 0 && !kF64 && TILE_HERM) {
       // split Hermitian: an item is a range of canonical 16 x 16 tiles
