@@ -55,6 +55,15 @@ struct tq_program {
   tq::DevBuf blob, sops, sb64, sb32, sps;
   size_t o_kraus = 0, o_ops = 0, o_blk = 0, o_mem = 0, o_work = 0, o_spw = 0, blob_bytes = 0;
   bool owns = true;  // standalone programs own their buffers
+  // tq_program_run replays the program's whole launch sequence as a CUDA
+  // graph, captured once per (rho, Hermitian-mode entry flags): the graph
+  // bakes in the state's buffer and the per-block Hermitian decisions
+  mutable cudaGraphExec_t g_exec = nullptr;
+  mutable cudaStream_t g_capture = nullptr;  // private stream the graph is captured on
+  mutable const void* g_rho = nullptr;
+  mutable int g_key = -1;                    // herm allowed | lower stale on entry << 1
+  mutable bool g_lower_after = false;
+  mutable unsigned long long g_launches = 0;
 };
 
 

@@ -739,7 +739,50 @@ tq_status tq_program_run(tq_state* s, const tq_program* p) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
   if (!p || p->n != s->n || p->prec != s->prec) return TQ_ERR_ARG;
-  return enqueue_program(s, *p);
+  if (s->prof_on) return enqueue_program(s, *p);  // per-launch events: launch directly
+  const int key = (s->herm_mode && s->herm_ok ? 1 : 0) | (s->lower_stale ? 2 : 0);
+  if (!(p->g_exec && p->g_rho == s->rho && p->g_key == key)) {
+    // (re)capture the launch sequence on a private stream; the state's flags
+    // and launch count advance as if it ran, which is what the graph does
+    if (p->g_exec) {  // an earlier launch may still run on any stream (rare path)
+      cudaDeviceSynchronize();
+      cudaGraphExecDestroy(p->g_exec);
+    }
+    p->g_exec = nullptr;
+    if (!p->g_capture && cudaStreamCreateWithFlags(&p->g_capture, cudaStreamNonBlocking) != cudaSuccess) {
+      p->g_capture = nullptr;
+      return enqueue_program(s, *p);
+    }
+    const bool lower0 = s->lower_stale;
+    const uint64_t l0 = s->launches;
+    cudaStream_t real = s->stream;
+    s->stream = p->g_capture;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->g_capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      st = enqueue_program(s, *p);
+      e = cudaStreamEndCapture(p->g_capture, &g);
+    }
+    s->stream = real;
+    if (e == cudaSuccess && st == TQ_OK) e = cudaGraphInstantiate(&p->g_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || st != TQ_OK || !p->g_exec) {  // not capturable here: run directly
+      cudaGetLastError();
+      p->g_exec = nullptr;
+      s->lower_stale = lower0;
+      s->launches = l0;
+      s->poisoned = false;
+      return enqueue_program(s, *p);
+    }
+    p->g_rho = s->rho;
+    p->g_key = key;
+    p->g_lower_after = s->lower_stale;
+    p->g_launches = s->launches - l0;
+  } else {
+    s->lower_stale = p->g_lower_after;
+    s->launches += p->g_launches;
+  }
+  return cuda_fail(s, cudaGraphLaunch(p->g_exec, s->stream));
 }
 
 tq_status tq_program_info(const tq_program* p, size_t* n_ops, size_t* n_blocks, int* max_width,
@@ -754,6 +797,14 @@ tq_status tq_program_info(const tq_program* p, size_t* n_ops, size_t* n_blocks, 
 
 void tq_program_free(tq_program* p) {
   if (!p) return;
+  if (p->g_exec) {
+    cudaDeviceSynchronize();  // its launches may still run on any stream
+    cudaGraphExecDestroy(p->g_exec);
+  }
+  if (p->g_capture) {
+    cudaStreamSynchronize(p->g_capture);
+    cudaStreamDestroy(p->g_capture);
+  }
   for (DevBuf* b : {&p->blob, &p->sops, &p->sb64, &p->sb32, &p->sps}) free_buf(*b);
   delete p;
 }
