@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_reduce(const char* arena, co
 }
 
 template <typename T2>
-inline size_t apply_smem() {
+__host__ __device__ constexpr size_t apply_smem() {
   return kSEntries * sizeof(T2) + kResidentBytes;
 }
 

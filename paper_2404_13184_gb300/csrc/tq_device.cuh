@@ -2,6 +2,8 @@
 // translation units (sm_103a).
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -144,6 +146,16 @@ cudaError_t launch_sample(const double* p, int n, double* cdf, const double* u, 
 // --- apply kernels (tq_apply.cu) ------------------------------------------
 // One pass of a fused block over vec(rho). S: 4^K x 4^K superoperator,
 // row-major (double2 for FP64 states, float2 for split states).
+// Small registers: all blocks of a program as one kernel on a thread-block
+// cluster with vec(rho) in distributed shared memory (tq_cluster.cu).
+// eligible: n <= 8, widths <= 2, >= 2 blocks. cluster_block_table: the
+// device table of blocks (bytes, to upload): width, qubits and superoperator
+// offset in the fused table `sb` (FP64 or FP32 by precision).
+bool cluster_program_eligible(int n, int max_width, size_t n_blocks);
+void cluster_block_table(const std::vector<ApplyParams>& params, const std::vector<long long>& sb_off,
+                         std::vector<unsigned char>* out);
+cudaError_t launch_cluster_program(void* rho, int precision, int n, const void* sb, const void* tab, int n_blocks,
+                                   cudaStream_t st);
 cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyParams& p,
                          int num_sms, cudaStream_t st, const SparseBlock* sparse = nullptr);
 

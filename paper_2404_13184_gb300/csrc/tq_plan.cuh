@@ -64,6 +64,9 @@ struct tq_program {
   mutable int g_key = -1;                    // herm allowed | lower stale on entry << 1
   mutable bool g_lower_after = false;
   mutable unsigned long long g_launches = 0;
+  // device table of the blocks for the cluster path (small registers)
+  mutable tq::DevBuf g_blk;
+  mutable bool g_blk_ready = false;
 };
 
 

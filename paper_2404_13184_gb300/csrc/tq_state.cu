@@ -347,6 +347,15 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
   });
   if (e == cudaSuccess)
     e = timed(s, K_FUSE, 1, [&] { return launch_fuse(sops, d_ops, d_blk, d_mem, d_work, P.n_work, sb64, sb32, s->stream); });
+  if (e == cudaSuccess && s->herm_mode && s->herm_ok && !s->prof_on && P.g_blk_ready) {
+    // small register: every block in one cluster kernel (Hermitian mode; the
+    // kernel builds its own row lists, so no compression pass)
+    s->launches += 1;
+    s->lower_stale = true;
+    e = launch_cluster_program(s->rho, s->prec, s->n, s->prec == TQ_FP64 ? (const void*)sb64 : (const void*)sb32,
+                               P.g_blk.ptr, (int)P.params.size(), s->stream);
+    return cuda_fail(s, e);
+  }
   SparseBlock* sps = static_cast<SparseBlock*>(P.sps.ptr);
   if (e == cudaSuccess && P.n_sparse > 0)
     e = timed(s, K_PACK, 1, [&] {
@@ -740,6 +749,14 @@ tq_status tq_program_run(tq_state* s, const tq_program* p) {
   if (st != TQ_OK) return st;
   if (!p || p->n != s->n || p->prec != s->prec) return TQ_ERR_ARG;
   if (s->prof_on) return enqueue_program(s, *p);  // per-launch events: launch directly
+  if (!p->g_blk_ready && cluster_program_eligible(p->n, p->max_width, p->params.size())) {
+    std::vector<unsigned char> tab;
+    cluster_block_table(p->params, p->sb_off, &tab);
+    cudaError_t e = grow(p->g_blk, tab.size(), nullptr, false);
+    if (e == cudaSuccess) e = cudaMemcpy(p->g_blk.ptr, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    p->g_blk_ready = true;
+  }
   const int key = (s->herm_mode && s->herm_ok ? 1 : 0) | (s->lower_stale ? 2 : 0);
   if (!(p->g_exec && p->g_rho == s->rho && p->g_key == key)) {
     // (re)capture the launch sequence on a private stream; the state's flags
@@ -805,7 +822,7 @@ void tq_program_free(tq_program* p) {
     cudaStreamSynchronize(p->g_capture);
     cudaStreamDestroy(p->g_capture);
   }
-  for (DevBuf* b : {&p->blob, &p->sops, &p->sb64, &p->sb32, &p->sps}) free_buf(*b);
+  for (DevBuf* b : {&p->blob, &p->sops, &p->sb64, &p->sb32, &p->sps, &p->g_blk}) free_buf(*b);
   delete p;
 }
 

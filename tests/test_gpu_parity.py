@@ -277,6 +277,28 @@ def test_max_size_16q_factorised_split(tq):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("n,width", [(3, 1), (6, 2), (8, 2), (6, 0)])
+def test_small_register_program_runs_on_a_cluster(tq, precision, n, width):
+    # n <= 8 and widths <= 2: tq_program_run applies every block in ONE
+    # kernel on a thread-block cluster (cluster barriers between blocks);
+    # the second run replays the captured graph
+    c = W.random_noisy_circuit(n, 60, 300 + n, gate_set=("h", "rx", "rz", "cx", "su2", "rzz"))
+    prog = tq.DeviceProgram(n, c.ops, width=width, precision=precision)
+    assert prog.n_blocks >= 2 and prog.max_width <= 2
+    want = O.run_circuit(n, c.ops)
+    tol = TOL64 if precision == "fp64" else 2e-6
+    with tq.State(n, precision) as st:
+        for _ in range(2):
+            st.reset()
+            l0 = st.launch_count()
+            st.run_program(prog)
+            assert st.launch_count() - l0 == 3            # superoperator build, fusion, the cluster kernel
+            assert maxabs(st.rho(), want) < tol
+            assert abs(st.trace().real - O.trace(want).real) < (TOL64 if precision == "fp64" else 1e-5)
+    prog.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_device_program_equals_host_call(tq, precision):
     import torch
     n = 9
