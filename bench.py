@@ -71,7 +71,9 @@ def fp64_peak_tflops(sm_mhz: float) -> float:
 def kernel_source_sha(symbol: str):
     """sha256 (first 16 hex digits) of a kernel's definition in csrc/ (from its
     `__global__` to the closing brace of its body) together with the shared
-    device helpers in tq_device.cuh: changes when the kernel's code does."""
+    device types and helpers of tq_device.cuh (the part before its launcher
+    declarations, #include lines left out): changes when the kernel's code
+    does."""
     csrc = os.path.join(ROOT, "paper_2404_13184_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if not name.endswith((".cu", ".cuh")):
@@ -89,7 +91,8 @@ def kernel_source_sha(symbol: str):
             if depth == 0:
                 break
             k += 1
-        helpers = open(os.path.join(csrc, "tq_device.cuh")).read()
+        helpers = open(os.path.join(csrc, "tq_device.cuh")).read().split("// --- kernel launchers")[0]
+        helpers = "\n".join(l for l in helpers.splitlines() if not l.startswith("#include"))
         return hashlib.sha256((text[start:k + 1] + helpers).encode()).hexdigest()[:16]
     return None
 
