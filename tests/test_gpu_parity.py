@@ -424,3 +424,25 @@ def test_split_hermitian_mode_matches_oracle(tq, n, width):
     assert maxabs(ra, want) < 2e-6
     assert maxabs(ra, rb) < 2e-6
     assert maxabs(za, [O.expect_z(want, m) for m in masks]) < 1e-5
+
+
+def test_split_precision_bounds_tfim_8q(tq):
+    # the split path's stated bounds on the 8-qubit ring TFIM (30 Trotter
+    # steps, 900 noisy gates) against the oracle: <Z0 Z1> after every step,
+    # every entry of rho, the trace drift before renormalisation, and the
+    # most negative eigenvalue (the oracle's state is positive to 1e-12)
+    n = 8
+    c = W.tfim_ring(n, 30)
+    rho = O.zero_state(n)
+    with tq.State(n, "split") as st:
+        for a, b in c.steps:
+            for op in c.ops[a:b]:
+                rho = O.apply_op(rho, op)
+            st.run(c.ops[a:b], width=-1)
+            assert abs(st.expect_z([3])[0] - O.expect_z(rho, 3) / O.trace(rho).real) < 1e-5
+        got = st.rho()
+        tr = st.trace().real
+    assert np.min(np.linalg.eigvalsh(rho)) > -1e-12
+    assert maxabs(got, rho) < 2e-6
+    assert abs(tr - 1.0) < 1e-5
+    assert np.min(np.linalg.eigvalsh((got + got.conj().T) / 2)) > -1e-6
