@@ -226,7 +226,18 @@ tq_status tq_program_create(int n_qubits, int precision, const tq_op* ops, size_
 
 /* Enqueue the program on the state's stream (asynchronous). The state must
  * have the program's n and precision (TQ_ERR_ARG otherwise). One program
- * may be run on several states, but not concurrently on two streams. */
+ * may be run on several states, but not concurrently on two streams nor
+ * from two host threads at once.
+ *
+ * The whole launch sequence is captured once into a CUDA graph and
+ * replayed. The graph bakes in the state's density-matrix buffer and
+ * whether Hermitian mode applies on entry. A run with another buffer or
+ * other entry flags recaptures it; the first run after a change pays the
+ * capture. With profiling on (tq_profile_enable) the launches are made
+ * one by one instead. For registers of at most 8 qubits whose blocks are
+ * at most 2 qubits wide, the apply passes are one kernel on a
+ * thread-block cluster holding rho in distributed shared memory, with a
+ * cluster barrier between blocks (Sec. 3.1 apply step). */
 tq_status tq_program_run(tq_state* s, const tq_program* p);
 
 /* Number of ops, of fused blocks, widest block, and the bytes of its device
