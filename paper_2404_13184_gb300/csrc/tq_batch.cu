@@ -234,11 +234,11 @@ tq_status finalize(tq_batch* b) {
 
   const size_t smem = b->prec == TQ_FP64 ? apply_smem<double2>() : apply_smem<float2>();
   if (b->prec == TQ_FP64) {
-    e = cudaFuncSetAttribute(k_batch_apply<double2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<double2, true, true>, kThreads, smem);
+    e = cudaFuncSetAttribute(k_batch_apply<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<double2>, kThreads, smem);
   } else {
-    e = cudaFuncSetAttribute(k_batch_apply<float2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<float2, true, true>, kThreads, smem);
+    e = cudaFuncSetAttribute(k_batch_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->per_sm, k_batch_apply<float2>, kThreads, smem);
   }
   if (e != cudaSuccess) return to_status(e);
   b->per_sm = std::max(1, b->per_sm);
@@ -270,12 +270,12 @@ tq_status finalize(tq_batch* b) {
   const int grid = (int)std::max<size_t>(1, std::min<size_t>(b->n_items, (size_t)b->num_sms * b->per_sm));
   if (b->n_items > 0) {
     if (b->prec == TQ_FP64)
-      k_batch_apply<double2, true, true><<<grid, kThreads, smem, st>>>(
+      k_batch_apply<double2><<<grid, kThreads, smem, st>>>(
           static_cast<char*>(b->arena.ptr), static_cast<const BJob*>(b->djobs.ptr),
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
     else
-      k_batch_apply<float2, true, true><<<grid, kThreads, smem, st>>>(
+      k_batch_apply<float2><<<grid, kThreads, smem, st>>>(
           static_cast<char*>(b->arena.ptr), static_cast<const BJob*>(b->djobs.ptr),
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);

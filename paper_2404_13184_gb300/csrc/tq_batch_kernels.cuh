@@ -83,40 +83,32 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// One group of a width-K block: gather its 4^K entries, multiply by S
-// (shared memory), scatter back. GLOBAL: rho in global memory, loaded
-// through L2 only (other CTAs wrote it); else rho is the shared-memory copy.
-// HERM: t indexes the canonical groups (row rest <= column rest); entries
-// below the diagonal are read and written through their conjugate
-// transposes, as in the single-state kernels. Used for split states; FP64
-// blocks go through the row-list forms below.
-template <typename T2, int K, bool GLOBAL, bool HERM>
+// One canonical group of a width-K split block on the shared-memory copy of
+// rho (resident items): gather its 4^K entries, multiply by S (shared
+// memory), scatter back. t indexes the canonical groups (row rest <= column
+// rest); entries below the diagonal are read and written through their
+// conjugate transposes, as in the single-state kernels.
+template <typename T2, int K>
 __device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const ApplyParams& p, const T2* sS) {
   constexpr int D = 1 << (2 * K);
   bool self = false;
-  unsigned long long base = HERM ? canonical_group(t, p.n - K, &self) : t;
+  unsigned long long base = canonical_group(t, p.n - K, &self);
 #pragma unroll
   for (int i = 0; i < 2 * K; ++i) {
     const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
     base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
   }
-  // Hermitian mode works on 32-bit row / column indices (n <= 16):
-  // r = rows of base + row part of off[l], c likewise.
+  // row / column indices are 32-bit (n <= 16): r = rows of base + row part
+  // of off[l], c likewise
   const unsigned int rmask = (1u << p.n) - 1u;
   const unsigned int rb = (unsigned int)(base & rmask), cb = (unsigned int)(base >> p.n);
   T2 x[D];
 #pragma unroll
   for (int l = 0; l < D; ++l) {
-    unsigned long long e;
-    bool conj = false;
-    if (HERM) {
-      const unsigned int r = rb + (unsigned int)(p.off[l] & rmask), c = cb + (unsigned int)(p.off[l] >> p.n);
-      conj = r > c;
-      e = conj ? ((unsigned long long)c | ((unsigned long long)r << p.n)) : ((unsigned long long)r | ((unsigned long long)c << p.n));
-    } else {
-      e = base + p.off[l];
-    }
-    T2 v = GLOBAL ? Cx<T2>::ldcg(&rho[e]) : rho[e];
+    const unsigned int r = rb + (unsigned int)(p.off[l] & rmask), c = cb + (unsigned int)(p.off[l] >> p.n);
+    const bool conj = r > c;
+    T2 v = rho[conj ? ((unsigned long long)c | ((unsigned long long)r << p.n))
+                    : ((unsigned long long)r | ((unsigned long long)c << p.n))];
     if (conj) v.y = -v.y;
     x[l] = v;
   }
@@ -125,16 +117,12 @@ __device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const
     T2 acc = Cx<T2>::zero();
 #pragma unroll
     for (int j = 0; j < D; ++j) Cx<T2>::fma(acc, sS[i * D + j], x[j]);
-    if (HERM) {
-      const unsigned int r = rb + (unsigned int)(p.off[i] & rmask), c = cb + (unsigned int)(p.off[i] >> p.n);
-      if (r <= c) {
-        rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
-      } else if (!self) {  // a self-conjugate group writes its upper entries only
-        acc.y = -acc.y;
-        rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
-      }
-    } else {
-      rho[base + p.off[i]] = acc;
+    const unsigned int r = rb + (unsigned int)(p.off[i] & rmask), c = cb + (unsigned int)(p.off[i] >> p.n);
+    if (r <= c) {
+      rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+    } else if (!self) {  // a self-conjugate group writes its upper entries only
+      acc.y = -acc.y;
+      rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
     }
   }
 }
@@ -377,10 +365,11 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
   __syncthreads();
 }
 
-// RES_HERM / TILE_HERM: resident / tile items use Hermitian mode (must match
-// BJob::herm as set by batch_herm: <true, true> for both precisions; split
-// tile items then walk canonical 16 x 16 tiles).
-template <typename T2, bool RES_HERM, bool TILE_HERM>
+// Every job runs in Hermitian mode (canonical groups; BJob::herm is always
+// set by batch_herm). Resident items: FP64 row lists or split dense products
+// on the shared-memory copy of rho. Tile items: FP64 row lists over a range
+// of canonical groups; split walks a range of canonical 16 x 16 tiles.
+template <typename T2>
 __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const BJob* __restrict__ jobs,
                                                           const BBlk* __restrict__ blks,
                                                           const BItem* __restrict__ items, int n_items,
@@ -410,20 +399,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
         stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16);
         const ApplyParams& p = s_blk.p;
-        const unsigned long long total = RES_HERM ? p.n_canon : p.n_groups;
-        for (unsigned long long g = threadIdx.x; g < total; g += blockDim.x) {
+        for (unsigned long long g = threadIdx.x; g < p.n_canon; g += blockDim.x) {
           if constexpr (kF64) {
             double2* sR64 = reinterpret_cast<double2*>(sR);
             const double2* val = reinterpret_cast<const double2*>(sS);
             if (p.width == 1)
-              apply_group_lists_resident<1, RES_HERM>(sR64, (unsigned int)g, p, val, s_rl);
+              apply_group_lists_resident<1, true>(sR64, (unsigned int)g, p, val, s_rl);
             else
-              apply_group_lists_resident<2, RES_HERM>(sR64, (unsigned int)g, p, val, s_rl);
+              apply_group_lists_resident<2, true>(sR64, (unsigned int)g, p, val, s_rl);
           } else {
             if (p.width == 1)
-              apply_group<T2, 1, false, RES_HERM>(sR, g, p, sS);
+              apply_group<T2, 1>(sR, g, p, sS);
             else
-              apply_group<T2, 2, false, RES_HERM>(sR, g, p, sS);
+              apply_group<T2, 2>(sR, g, p, sS);
           }
         }
         __syncthreads();
@@ -449,42 +437,35 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
     }
     __syncthreads();
     const ApplyParams& p = s_blk.p;
-    if (*(volatile int*)err == 0 && !kF64 && TILE_HERM) {
-      // split Hermitian: an item is a range of canonical 16 x 16 tiles
-      const unsigned long long upt = 1ull << tiles16_log2(jb.tile_log2, p.width);
-      const unsigned long long Mt = (1ull << (p.n - p.width)) / 16;
-      const unsigned long long total = Mt * (Mt + 1) / 2;
-      const unsigned long long u0 = (unsigned long long)it.tile0 * upt;
-      const unsigned long long u1 = min(total, u0 + (unsigned long long)it.ntiles * upt);
-      float2* rho32 = reinterpret_cast<float2*>(rho);
-      const float2* s32 = reinterpret_cast<const float2*>(sS);
-      for (unsigned long long u = u0; u < u1; ++u) {
-        if (p.width == 1)
-          apply_tile16<1>(rho32, u, p, s32, s_t16);
-        else
-          apply_tile16<2>(rho32, u, p, s32, s_t16);
-      }
-    } else if (*(volatile int*)err == 0) {
-      const unsigned long long gpt = 1ull << (jb.tile_log2 - 2 * p.width);  // groups per tile
-      const unsigned long long total = TILE_HERM ? p.n_canon : p.n_groups;
-      const unsigned long long g0 = (unsigned long long)it.tile0 * gpt;
-      const unsigned long long g1 = min(total, g0 + (unsigned long long)it.ntiles * gpt);
-      for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-        if constexpr (kF64) {
-          // the resident buffer is free in tile items: it holds the
-          // threads' operand columns (16 x kThreads entries = 64 KiB)
-          double2* mine = reinterpret_cast<double2*>(sR) + threadIdx.x;
-          const double2* val = reinterpret_cast<const double2*>(sS);
-          double2* rho64 = reinterpret_cast<double2*>(rho);
+    if (*(volatile int*)err == 0) {
+      if constexpr (kF64) {
+        // a range of canonical groups; the resident buffer is free in tile
+        // items and holds the threads' operand columns (16 x kThreads
+        // entries = 64 KiB)
+        const unsigned long long gpt = 1ull << (jb.tile_log2 - 2 * p.width);  // groups per tile
+        const unsigned long long g0 = (unsigned long long)it.tile0 * gpt;
+        const unsigned long long g1 = min(p.n_canon, g0 + (unsigned long long)it.ntiles * gpt);
+        double2* mine = reinterpret_cast<double2*>(sR) + threadIdx.x;
+        const double2* val = reinterpret_cast<const double2*>(sS);
+        double2* rho64 = reinterpret_cast<double2*>(rho);
+        for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
           if (p.width == 1)
-            apply_group_lists_global<1, TILE_HERM>(rho64, g, p, val, s_rl, mine);
+            apply_group_lists_global<1, true>(rho64, g, p, val, s_rl, mine);
           else
-            apply_group_lists_global<2, TILE_HERM>(rho64, g, p, val, s_rl, mine);
-        } else {
+            apply_group_lists_global<2, true>(rho64, g, p, val, s_rl, mine);
+        }
+      } else {
+        // a range of canonical 16 x 16 tiles
+        const unsigned long long upt = 1ull << tiles16_log2(jb.tile_log2, p.width);
+        const unsigned long long Mt = (1ull << (p.n - p.width)) / 16;
+        const unsigned long long total = Mt * (Mt + 1) / 2;
+        const unsigned long long u0 = (unsigned long long)it.tile0 * upt;
+        const unsigned long long u1 = min(total, u0 + (unsigned long long)it.ntiles * upt);
+        for (unsigned long long u = u0; u < u1; ++u) {
           if (p.width == 1)
-            apply_group<T2, 1, true, false>(rho, g, p, sS);
+            apply_tile16<1>(rho, u, p, sS, s_t16);
           else
-            apply_group<T2, 2, true, false>(rho, g, p, sS);
+            apply_tile16<2>(rho, u, p, sS, s_t16);
         }
       }
     }

@@ -232,11 +232,11 @@ tq_status tq_server_create(int precision, void* cuda_stream, size_t rho_budget_b
     s->tab_mem.cap = s->tab_budget;
     const size_t smem = precision == TQ_FP64 ? apply_smem<double2>() : apply_smem<float2>();
     if (precision == TQ_FP64) {
-      e = cudaFuncSetAttribute(k_batch_apply<double2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<double2, true, true>, kThreads, smem);
+      e = cudaFuncSetAttribute(k_batch_apply<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<double2>, kThreads, smem);
     } else {
-      e = cudaFuncSetAttribute(k_batch_apply<float2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2, true, true>, kThreads, smem);
+      e = cudaFuncSetAttribute(k_batch_apply<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s->per_sm, k_batch_apply<float2>, kThreads, smem);
     }
   }
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev0);
@@ -412,12 +412,12 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
     int* ticket = static_cast<int*>(s->ctl.ptr);
     const int grid = (int)std::max<size_t>(1, std::min<size_t>(items.size(), (size_t)s->num_sms * s->per_sm));
     if (s->prec == TQ_FP64)
-      k_batch_apply<double2, true, true><<<grid, kThreads, apply_smem<double2>(), s->stream>>>(
+      k_batch_apply<double2><<<grid, kThreads, apply_smem<double2>(), s->stream>>>(
           static_cast<char*>(s->rho_mem.ptr), static_cast<const BJob*>(s->djobs.ptr), static_cast<const BBlk*>(s->dblks.ptr),
           static_cast<const BItem*>(s->ditems.ptr), (int)items.size(), static_cast<int*>(s->counters.ptr), ticket,
           ticket + 32, s->max_spin);
     else
-      k_batch_apply<float2, true, true><<<grid, kThreads, apply_smem<float2>(), s->stream>>>(
+      k_batch_apply<float2><<<grid, kThreads, apply_smem<float2>(), s->stream>>>(
           static_cast<char*>(s->rho_mem.ptr), static_cast<const BJob*>(s->djobs.ptr), static_cast<const BBlk*>(s->dblks.ptr),
           static_cast<const BItem*>(s->ditems.ptr), (int)items.size(), static_cast<int*>(s->counters.ptr), ticket,
           ticket + 32, s->max_spin);
