@@ -56,7 +56,11 @@ typedef struct tq_state tq_state; /* opaque; owns the device copy of vec(rho) */
 typedef enum {
   TQ_FP64 = 0,  /* rho complex128, superoperator products in FP64 */
   TQ_SPLIT = 1  /* rho complex64, products in FP32 (FP64 superoperator build,
-                   fusion, trace renormalisation and readouts) */
+                   fusion, trace renormalisation and readouts). Width-2
+                   blocks on a Hermitian state run on the tcgen05 tensor
+                   cores: each FP32 operand split into three BF16 terms,
+                   six term products accumulated in FP32 (Sec. 3.2 maps the
+                   update onto tensor cores) */
 } tq_precision;
 
 typedef enum {
@@ -199,6 +203,11 @@ tq_status tq_run_circuit(tq_state* s, const tq_op* ops, size_t n_ops, int max_fu
                          size_t* n_blocks_out);
 
 /* ---- readouts (FP64 reductions over the diagonal, Sec. 2.1) ------------ */
+/* The synchronising readouts (tq_trace, tq_expect_z, tq_probs,
+ * tq_probs_readout, tq_sample, tq_measure, tq_get_rho) of a TQ_SPLIT state
+ * that has run a tensor-core pass also report TQ_ERR_TIMEOUT, and poison the
+ * state, if a bounded wait for that pass's MMAs ran out (a pass that did not
+ * complete; its results are not valid). */
 
 /* Tr(rho) = sum_x rho[x][x]. */
 tq_status tq_trace(tq_state* s, double* re, double* im);

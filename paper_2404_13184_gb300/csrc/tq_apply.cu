@@ -485,7 +485,7 @@ cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyPar
     const float2* s = static_cast<const float2*>(S);
     if (p.herm) {
       if (p.width == 1) return run_herm_tiled_split<1>(r, s, p, num_sms, st);
-      if (p.width == 2) return run_herm_tiled_split<2>(r, s, p, num_sms, st);
+      if (p.width == 2) return launch_herm_tc2(r, s, p, num_sms, st);
       return cudaErrorInvalidValue;  // split Hermitian mode covers widths 1 and 2
     }
     switch (p.width) {

@@ -158,5 +158,11 @@ cudaError_t launch_cluster_program(void* rho, int precision, int n, const void* 
                                    cudaStream_t st);
 cudaError_t launch_apply(void* rho, int precision, const void* S, const ApplyParams& p,
                          int num_sms, cudaStream_t st, const SparseBlock* sparse = nullptr);
+// Split states, width 2, Hermitian mode: the pass on the tcgen05 tensor
+// cores (tq_apply_tc.cu); needs n - 2 >= 4.
+cudaError_t launch_herm_tc2(float2* rho, const float2* S, const ApplyParams& p, int num_sms, cudaStream_t st);
+// Bounded tensor-core waits that gave up since the last call (any state on
+// the current device); clears the count. Synchronises `st`.
+cudaError_t tc_take_timeouts(unsigned int* count, cudaStream_t st);
 
 }  // namespace tq

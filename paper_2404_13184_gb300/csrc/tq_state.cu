@@ -52,6 +52,7 @@ struct tq_state {
   bool herm_mode = true;     // allowed by the caller
   bool herm_ok = true;       // rho is known to be Hermitian
   bool lower_stale = false;  // entries with row > column are out of date
+  bool tc_used = false;      // a tensor-core pass (bounded waits) was enqueued
   uint64_t launches = 0;
   bool prof_on = false;
   std::vector<Pending> pending;
@@ -123,6 +124,21 @@ size_t entry_bytes(int prec) { return prec == TQ_FP64 ? 16 : 8; }
 tq_status check_state(tq_state* s) {
   if (!s) return TQ_ERR_ARG;
   if (s->poisoned) return TQ_ERR_STATE;
+  return TQ_OK;
+}
+
+// End of a synchronising readout: CUDA errors poison the state, and so does
+// a tensor-core pass whose bounded wait gave up (its results are not valid).
+tq_status readout_done(tq_state* s, cudaError_t e) {
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (!s->tc_used) return TQ_OK;
+  unsigned int timeouts = 0;
+  e = tc_take_timeouts(&timeouts, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (timeouts) {
+    s->poisoned = true;
+    return TQ_ERR_TIMEOUT;
+  }
   return TQ_OK;
 }
 
@@ -387,6 +403,7 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
     if (!sparse) p.sparse = 0;
     const int kind = sparse ? K_SPARSE64 + p.width - 1 : (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
     const SparseBlock* spb = sparse ? sps + P.sp_slot[b] : nullptr;
+    if (herm && s->prec == TQ_SPLIT && p.width == 2) s->tc_used = true;
     e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream, spb); });
     if (s->prof_on) {  // per launch: the groups computed x (8 * 16^w flops, 2 * B * 4^w bytes) each
       const double per = (double)(1 << (2 * p.width));
@@ -523,7 +540,7 @@ tq_status reduce_impl(tq_state* s, const unsigned long long* masks, int n_masks,
   if (st != TQ_OK) return st;
   e = cudaMemcpyAsync(hout, d + kRedOut, (2 + n_masks) * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return cuda_fail(s, e);
+  if ((st = readout_done(s, e)) != TQ_OK) return st;
   std::memcpy(host_out, hout, (2 + n_masks) * sizeof(double));
   return TQ_OK;
 }
@@ -637,7 +654,7 @@ tq_status tq_get_rho(tq_state* s, double* out) {
     if ((st = tq_rho_device_ptr(s, &full)) != TQ_OK) return st;  // fills the lower triangle if needed
     e = cudaMemcpyAsync(out, s->rho, entries * 16, cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return cuda_fail(s, e);
+    return readout_done(s, e);
   }
   const size_t chunk = std::min<size_t>(entries, 1ull << 22);  // complex entries per pass
   if ((st = ensure(s, s->staging, chunk * 16)) != TQ_OK) return st;
@@ -653,7 +670,7 @@ tq_status tq_get_rho(tq_state* s, double* out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e);
   }
-  return TQ_OK;
+  return readout_done(s, cudaSuccess);
 }
 
 tq_status tq_set_rho(tq_state* s, const double* in) {
@@ -900,7 +917,7 @@ tq_status tq_probs(tq_state* s, double* out) {
   const size_t N = 1ull << s->n;
   cudaError_t e = cudaMemcpyAsync(out, s->probs.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  return cuda_fail(s, e);
+  return readout_done(s, e);
 }
 
 tq_status tq_probs_readout(tq_state* s, const double* e10, const double* e01, double* out) {
@@ -911,7 +928,7 @@ tq_status tq_probs_readout(tq_state* s, const double* e10, const double* e01, do
   const size_t N = 1ull << s->n;
   cudaError_t e = cudaMemcpyAsync(out, s->probs.ptr, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  return cuda_fail(s, e);
+  return readout_done(s, e);
 }
 
 tq_status tq_sample(tq_state* s, const double* u, int shots, const double* e10, const double* e01,
@@ -941,7 +958,7 @@ tq_status tq_sample(tq_state* s, const double* u, int shots, const double* e10, 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s->pin.ptr, dout, (size_t)shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return cuda_fail(s, e);
+  if ((st = readout_done(s, e)) != TQ_OK) return st;
   std::memcpy(outcomes, s->pin.ptr, (size_t)shots * sizeof(uint64_t));
   return TQ_OK;
 }
