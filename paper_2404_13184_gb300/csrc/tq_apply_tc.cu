@@ -32,14 +32,15 @@
 // groups), one CTA of 128 threads, one thread per group, several CTAs per
 // SM. Per unit t a thread:
 //   - has unit t's 16 entries in registers (loaded during unit t - 1),
-//     splits them into the three BF16 terms and writes its row of the A
-//     operand (shared memory, K-major, 8 x 16-byte core matrices, no
-//     swizzle);
+//     issues the loads of unit t + 1 into registers, splits unit t's
+//     entries into the three BF16 terms and writes its row of the A operand
+//     (shared memory, K-major, 8 x 16-byte core matrices, no swizzle);
 //   - after the CTA barrier, one thread issues the 12 MMAs of the unit
 //     (M = 128, N = 32, K = 16 each) into the CTA's 32-column tensor-memory
 //     accumulator and commits them to an mbarrier;
-//   - every thread issues the loads of unit t + 1 into registers, waits
-//     (bounded) for the MMAs, reads its row of D, adds x and stores.
+//   - every thread waits (bounded) for the MMAs, reads its row of D, adds x
+//     and stores. Groups are disjoint, so the early loads of unit t + 1
+//     never see an entry that unit t writes.
 // Index math is 32-bit (n <= 16, so a vec index fits): a group's rows and
 // columns are rb + {0, 2^q0, 2^q1, 2^q0 + 2^q1} and cb + the same.
 #include <algorithm>
@@ -271,8 +272,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
   for (; u < n_units; u += gridDim.x, phase ^= 1u) {
     const Group g = gn;
     float2 x[D];
-    // this unit's entries: the below-diagonal ones were read from their
-    // transposes (conjugate); split into the A operand row
+#pragma unroll
+    for (int l = 0; l < D; ++l) x[l] = xn[l];
+    if (u + gridDim.x < n_units) {
+      gn = group_of(u + gridDim.x);
+      load(gn, xn);
+    }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       uint32_t tw[3][4];
@@ -281,7 +286,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
         const int l = 4 * c + e;
         bool up;
         (void)entry_index(g, l, b0, b1, N, &up);
-        x[l] = xn[l];
         if (!up) x[l].y = -x[l].y;
         uint32_t tt[3];
         split3(x[l].x, x[l].y, tt);
@@ -310,12 +314,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                    : "memory");
-    }
-    // the next unit's loads overlap the MMAs (groups are disjoint, so they
-    // never see an entry this unit writes)
-    if (u + gridDim.x < n_units) {
-      gn = group_of(u + gridDim.x);
-      load(gn, xn);
     }
     if (!bar_wait(bar, phase)) {
       atomicAdd(&g_tc_timeouts, 1u);
