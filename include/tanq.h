@@ -202,6 +202,18 @@ tq_status tq_apply_kraus(tq_state* s, const int* qubits, int k, int m, const dou
 tq_status tq_run_circuit(tq_state* s, const tq_op* ops, size_t n_ops, int max_fuse_width,
                          size_t* n_blocks_out);
 
+/* Failure-detection hook for tests (the paper has no counterpart): the
+ * MMA-completion waits of the split tensor-core pass (width-2 blocks of a
+ * TQ_SPLIT state in Hermitian mode) give up after max_tries try-wait rounds
+ * (0 restores the default, ~seconds); with skip_mma != 0 the passes
+ * launched afterwards issue neither their MMAs nor the commit, so their
+ * first wait runs out with nothing in flight and the next synchronising
+ * readout of that state returns TQ_ERR_TIMEOUT (the state is poisoned)
+ * while the CUDA context stays usable. Process-wide; read at each launch
+ * (a device program's captured graph keeps the values it was captured
+ * with). TQ_ERR_ARG if max_tries < 0. */
+tq_status tq_test_tc_wait_limit(long long max_tries, int skip_mma);
+
 /* ---- readouts (FP64 reductions over the diagonal, Sec. 2.1) ------------ */
 /* The synchronising readouts (tq_trace, tq_expect_z, tq_probs,
  * tq_probs_readout, tq_sample, tq_measure, tq_get_rho) of a TQ_SPLIT state

@@ -81,6 +81,7 @@ _SIGNATURES = [
     ("tq_batch_set_tile", c_int, [c_void_p, c_int, c_int]),
     ("tq_batch_run", c_int, [c_void_p]),
     ("tq_batch_test_wait_limit", c_int, [c_void_p, ctypes.c_longlong, c_int]),
+    ("tq_test_tc_wait_limit", c_int, [ctypes.c_longlong, c_int]),
     ("tq_batch_wait", c_int, [c_void_p]),
     ("tq_batch_result", c_int, [c_void_p, c_int, POINTER(c_double)]),
     ("tq_batch_get_rho", c_int, [c_void_p, c_int, POINTER(c_double)]),
@@ -344,6 +345,12 @@ class Server:
             self.free()
         except Exception:
             pass
+
+
+def test_tc_wait_limit(max_tries: int, skip_mma: bool = False):
+    """Failure-path test hook of the split tensor-core pass (see
+    tq_test_tc_wait_limit): max_tries 0 restores the default."""
+    _check(load().tq_test_tc_wait_limit(max_tries, 1 if skip_mma else 0), "tq_test_tc_wait_limit")
 
 
 def plan_fusion(n: int, ops, width: int, precision: str = "fp64"):

@@ -22,9 +22,11 @@
 //     and stores. Groups are disjoint, so the early loads of unit t + 1
 //     never see an entry that unit t writes.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "tq_device.cuh"
+#include "tanq.h"
 #include "tq_tc.cuh"
 
 namespace tq {
@@ -50,6 +52,10 @@ constexpr uint32_t kTmemCols = 32;
 constexpr int kCtasPerSm = 4;
 constexpr long long kMaxSpin = 1ll << 22;  // try_wait rounds before a wait gives up (~seconds)
 
+// Failure-path test settings (tq_test_tc_wait_limit), read at each launch.
+std::atomic<long long> g_test_max_tries{kMaxSpin};
+std::atomic<int> g_test_skip_mma{0};
+
 // This thread's group in a work unit: row and column bases (target bits
 // zero), whether it is canonical, whether it is self-conjugate.
 struct Group {
@@ -57,8 +63,12 @@ struct Group {
   bool active, self;
 };
 
+// max_tries: try_wait rounds before an MMA wait gives up; skip_mma (tests
+// of the failure path only): issue neither the MMAs nor their commit, so
+// the first wait runs out with nothing in flight.
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2* rho, const float2* __restrict__ S,
-                                                                           const __grid_constant__ ApplyParams p) {
+                                                                           const __grid_constant__ ApplyParams p,
+                                                                           long long max_tries, int skip_mma) {
   constexpr int D = 16;
   extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
@@ -139,12 +149,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
     fence_before_sync();
     __syncthreads();
     if (*s_abort) break;
-    if (tid == 0) {
+    if (tid == 0 && !skip_mma) {
       fence_after_sync();
       mma_split3(tmem, sbase + kOffA, kATermBytes, sbase + kOffB, kBTermBytes);
       commit(bar);
     }
-    if (!bar_wait(bar, phase, kMaxSpin)) {
+    if (!bar_wait(bar, phase, max_tries)) {
       atomicAdd(&g_tc_timeouts, 1u);
       *s_abort = 1;  // every thread leaves at the next unit's barrier
     }
@@ -174,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
   // after a timeout the unit's MMAs may still be in flight: wait for them
   // (bounded) before the tensor memory is released; the parity was toggled
   // once more after the unit that timed out (in the last unit too)
-  if (*s_abort && tid == 0) bar_wait(bar, phase ^ 1u, kMaxSpin);
+  if (*s_abort && tid == 0) bar_wait(bar, phase ^ 1u, max_tries);
   __syncthreads();
   if (w == 0) {
     fence_after_sync();
@@ -198,7 +208,7 @@ cudaError_t launch_herm_tc2(float2* rho, const float2* S, const ApplyParams& p, 
   const unsigned long long Mt = M / kTile, n_units = Mt * (Mt + 1);
   const int grid = (int)std::max<unsigned long long>(
       1, std::min<unsigned long long>(n_units, (unsigned long long)num_sms * kCtasPerSm));
-  k_apply_herm_tc2<<<grid, kThreads, kSmemBytes, st>>>(rho, S, p);
+  k_apply_herm_tc2<<<grid, kThreads, kSmemBytes, st>>>(rho, S, p, g_test_max_tries.load(), g_test_skip_mma.load());
   return cudaGetLastError();
 }
 
@@ -214,3 +224,10 @@ cudaError_t tc_take_timeouts(unsigned int* count, cudaStream_t st) {
 }
 
 }  // namespace tq
+
+extern "C" tq_status tq_test_tc_wait_limit(long long max_tries, int skip_mma) {
+  if (max_tries < 0) return TQ_ERR_ARG;
+  tq::g_test_max_tries.store(max_tries == 0 ? tq::kMaxSpin : max_tries);
+  tq::g_test_skip_mma.store(skip_mma ? 1 : 0);
+  return TQ_OK;
+}

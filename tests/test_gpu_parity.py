@@ -446,3 +446,30 @@ def test_split_precision_bounds_tfim_8q(tq):
     assert maxabs(got, rho) < 2e-6
     assert abs(tr - 1.0) < 1e-5
     assert np.min(np.linalg.eigvalsh((got + got.conj().T) / 2)) > -1e-6
+
+
+def test_split_tensor_core_wait_timeout_is_reported(tq):
+    # failure path of the split tensor-core pass: with its MMAs (and their
+    # commit) skipped, the bounded MMA wait runs out with nothing in flight;
+    # the kernel frees its tensor memory and returns, the next readout of the
+    # state reports TQ_ERR_TIMEOUT and poisons it, and the context stays usable
+    n = 9
+    c = W.tfim_ring(n, 1)
+    try:
+        tq.test_tc_wait_limit(2000, skip_mma=True)
+        with tq.State(n, "split") as st:
+            assert st.hermitian_mode()
+            st.run(c.ops, width=2)
+            with pytest.raises(tq.TqError) as e:
+                st.expect_z([3])
+            assert e.value.status == 5          # TQ_ERR_TIMEOUT
+            with pytest.raises(tq.TqError) as e:
+                st.trace()
+            assert e.value.status == 6          # TQ_ERR_STATE: poisoned
+    finally:
+        tq.test_tc_wait_limit(0, skip_mma=False)
+    want = O.run_circuit(n, c.ops)
+    with tq.State(n, "split") as st:
+        st.run(c.ops, width=2)
+        assert maxabs(st.rho(), want) < 2e-6
+        assert abs(st.trace().real - 1.0) < 1e-5
