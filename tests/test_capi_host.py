@@ -263,3 +263,11 @@ def test_register_size_limits_are_checked_before_any_gpu_work(lib):
         assert lib.tq_create(n, 0, None, B.ctypes.byref(h)) == 1
         assert not h.value
     assert lib.tq_create(3, 7, None, B.ctypes.byref(h)) == 1          # unknown precision
+
+
+def test_tensor_core_wait_hook_arguments(lib):
+    # the failure-path hook of the split tensor-core pass only sets host-side
+    # launch values: negative limits are rejected, 0 restores the default
+    assert lib.tq_test_tc_wait_limit(-1, 0) == 1          # TQ_ERR_ARG
+    assert lib.tq_test_tc_wait_limit(1000, 1) == 0
+    assert lib.tq_test_tc_wait_limit(0, 0) == 0
