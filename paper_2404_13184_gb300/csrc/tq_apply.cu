@@ -223,7 +223,9 @@ cudaError_t run_sparse(double2* rho, const SparseBlock* sp, const ApplyParams& p
   return cudaGetLastError();
 }
 
-// Hermitian mode for split states (widths 1, 2). The pass is HBM-bound, so
+// Hermitian mode for split states on the CUDA cores: width 1 (width-2 blocks
+// run on the tensor cores, tq_apply_tc.cu; the template still covers K = 2,
+// with the same tile walk as the tensor-core kernel). The pass is HBM-bound, so
 // the canonical groups are walked in T x T tiles: row-rest a in
 // [ta T, ta T + T), column-rest b in [tb T, tb T + T), ta <= tb, one thread
 // per group; a warp covers 8 consecutive a by 4 consecutive b. Entries on or
