@@ -287,6 +287,39 @@ def cpu_sample_rate(pairs: int = 1):
     return raw * 4.0 ** (-(N_QUBITS - n)), raw, dt
 
 
+def oracle_prefix_time(n, ops, budget_s, min_ops=3):
+    """The CPU oracle run op by op from |0><0| on an n-qubit register until
+    `budget_s` seconds have passed (and at least `min_ops` ops ran) or the
+    ops run out: (ops done, seconds; the initial state is not timed)."""
+    from oracle import dm_oracle
+    rho = dm_oracle.zero_state(n)
+    t0 = time.perf_counter()
+    done = 0
+    for op in ops:
+        rho = dm_oracle.apply_op(rho, op)
+        done += 1
+        if done >= min_ops and time.perf_counter() - t0 >= budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline_circuits(circuits, budget_per_n=1.5):
+    """Oracle time of a set of circuits, estimated from a bounded sample: per
+    register size n, the first ops of the first circuit of that size run
+    until `budget_per_n` seconds (or the circuit ends) give the oracle's time
+    per op at n; the estimate is that time x the ops of every circuit of
+    size n. Returns (estimated seconds for all circuits, sample text)."""
+    per_op, parts = {}, []
+    for c in circuits:
+        if c.n not in per_op:
+            done, dt = oracle_prefix_time(c.n, c.ops, budget_per_n)
+            per_op[c.n] = dt / done
+            parts.append(f"{done} ops at n={c.n}")
+    total = sum(per_op[c.n] * len(c.ops) for c in circuits)
+    return total, ("oracle time per op measured per register size on a prefix of one circuit (" + ", ".join(parts)
+                   + "), times the ops of every circuit")
+
+
 def split_accuracy(tq, n=8, steps=30):
     """Error of the split path on the same ring TFIM at 8 qubits (30 Trotter
     steps), against the FP64 GPU path (held to the oracle by the parity
@@ -319,7 +352,8 @@ def autotune_cache():
     return os.path.join(ROOT, "paper_2404_13184_gb300", "autotune_cache.txt")
 
 
-def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11, reference=None):
+def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11, reference=None,
+              with_cpu=False):
     """Batched sweep: `count` independent noisy circuits (n ~ U{4..11}, depth
     ~ U{50..500}, {H, RZ, RX, CX}, per-circuit depolarising p) in one
     persistent launch per run (a CUDA graph replay), tile and fusion width per
@@ -374,7 +408,12 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
                 "bytes_per_run": work["bytes"], "peak_source": f"hbm_gbs ({src})"}
     gates = sum(c.n_gates for c in circuits)
+    cpu = None
+    if with_cpu:
+        est, sample = cpu_baseline_circuits(circuits)
+        cpu = {"value": count / est, "unit": "circuits/s", "cores": 1, "kind": "oracle", "sample": sample}
     return {"ms_per_run": ms, "circuits_per_s": count / (ms / 1e3), "gates_per_s": gates / (ms / 1e3),
+            "cpu_baseline": cpu,
             "circuits": count, "noisy_gates": gates, "items": info["items"], "rho_bytes": info["rho_bytes"],
             "autotune": {str(n): {"tile_log2": t, "width": w, "ms": round(m, 3)} for n, (t, w, m) in tuned.items()},
             "autotune_s": t_tune, "accuracy": err, "roofline": roof, "results": results}
@@ -449,7 +488,7 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
             "sustainable_rate_per_s": len(lat) / max(busy, 1e-9)}
 
 
-def run_plain6(tq, torch, steps, warmup):
+def run_plain6(tq, torch, steps, warmup, with_cpu=True):
     """6 qubits, 200 random noisy gates, FP64, no fusion (every gate and
     every channel is its own pass): the single-state device program (one
     launch per pass) and the batch engine (one resident CTA for the whole
@@ -493,6 +532,15 @@ def run_plain6(tq, torch, steps, warmup):
     out["batch_engine"] = {"ms_per_circuit": ms, "gates_per_s": c.n_gates / (ms / 1e3)}
     # the two GPU paths (different kernels, both held to the oracle by the tests)
     out["accuracy"] = {"max_abs_z_diff_program_vs_batch": max(abs(a - b) for a, b in zip(z_gpu, z_b))}
+    if with_cpu:
+        from oracle import dm_oracle
+        reps, t0 = 0, time.perf_counter()
+        while reps < 3 or time.perf_counter() - t0 < 2.0:
+            dm_oracle.run_circuit(c.n, c.ops)
+            reps += 1
+        dt = (time.perf_counter() - t0) / reps
+        out["cpu_baseline"] = {"value": c.n_gates / dt, "unit": "noisy gates/s", "ms_per_circuit": dt * 1e3,
+                               "cores": 1, "kind": "oracle", "sample": f"the whole circuit, {reps} runs"}
     return out
 
 
@@ -526,7 +574,7 @@ def run_purify(tq, precision):
     return out
 
 
-def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12):
+def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12, with_cpu=False):
     """Layered thermal-relaxation workload (n = 12: 2^24 entries, 2000 gates):
     time of the whole circuit per fusion width (0 = unfused plain path) and
     the max-abs difference of <Z_i> and sampled vec(rho) entries to the
@@ -558,7 +606,15 @@ def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12):
     base = out[str(widths[0])]["ms"]
     for w in out:
         out[w]["speedup_vs_unfused"] = base / out[w]["ms"]
-    return {"n_qubits": n, "noisy_gates": c.n_gates, "widths": out}
+    line = {"n_qubits": n, "noisy_gates": c.n_gates, "widths": out}
+    if with_cpu:
+        done, dt = oracle_prefix_time(n, c.ops, 20.0)
+        est = dt * len(c.ops) / done
+        line["cpu_baseline"] = {"value": c.n_gates / est, "unit": "noisy gates/s", "ms_per_circuit": est * 1e3,
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"first {done} of the circuit's {len(c.ops)} ops (gates and channels), "
+                                          f"{dt:.1f} s, time scaled by {len(c.ops)}/{done}"}
+    return line
 
 
 def reference_arm(args, world, rank):
@@ -633,15 +689,15 @@ def main():
 
     if args.workload == "layered12":
         precs = ["fp64", "split"] if args.precision == "both" else [args.precision]
-        for prec in precs:
-            r = run_layered(tq, torch, prec)
+        for i, prec in enumerate(precs):
+            r = run_layered(tq, torch, prec, with_cpu=i == 0 and rank == 0 and not args.no_cpu_baseline)
             if rank == 0:
                 print(json.dumps({"metric": "layered thermal circuit: time per fusion width", "workload":
                                   "layered-thermal-12q-2000g", "dtype": "f64" if prec == "fp64" else "f32", **r}),
                       flush=True)
         return 0
     if args.workload == "plain6":
-        r = run_plain6(tq, torch, max(args.steps, 20), args.warmup)
+        r = run_plain6(tq, torch, max(args.steps, 20), args.warmup, with_cpu=rank == 0 and not args.no_cpu_baseline)
         if rank == 0:
             print(json.dumps({"metric": "plain 6-qubit circuit, unfused: noisy gates/s", "workload":
                               "plain-6q-200g (FP64, no fusion)", "dtype": "f64", **r}), flush=True)
@@ -661,7 +717,8 @@ def main():
             if args.workload == "sweep":
                 lo, hi = (int(v) for v in args.sweep_qubits.split("-"))
                 r = run_sweep(tq, torch, prec, args.steps, args.warmup, count=args.sweep_count, n_min=lo, n_max=hi,
-                              reference=fp64_results if prec == "split" else None)
+                              reference=fp64_results if prec == "split" else None,
+                              with_cpu=prec == precs[0] and rank == 0 and not args.no_cpu_baseline)
                 res = r.pop("results")
                 if prec == "fp64":
                     fp64_results = res
