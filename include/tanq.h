@@ -423,8 +423,11 @@ void tq_server_free(tq_server* s);
  * device array inside the library, present on every GPU that loads the
  * library until the process exits. Limits: 1 <= n_masks <= 16 and
  * 1 <= n_qubits <= 16; larger requests return TQ_ERR_ARG. The first call on
- * each device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. All calls share the one
+ * each device looks up that array's device address (cudaGetSymbolAddress)
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture, and do not call this entry point again on a device after
+ * cudaDeviceReset (a new context may place the array elsewhere, and the kept
+ * address would then be stale). All calls share the one
  * array, so calls whose work overlaps on the GPU (different streams, or
  * different host threads without ordering) race and give wrong results;
  * order them on one stream. Nothing in the array needs clearing between

@@ -154,10 +154,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
       mma_split3(tmem, sbase + kOffA, kATermBytes, sbase + kOffB, kBTermBytes);
       commit(bar);
     }
-    if (!bar_wait(bar, phase, max_tries)) {
+    const bool waited = bar_wait(bar, phase, max_tries);
+    if (!waited) {
       atomicAdd(&g_tc_timeouts, 1u);
       *s_abort = 1;  // every thread leaves at the next unit's barrier
     }
+    // a warp reads the accumulator (tcgen05.ld is warp-collective) only if
+    // every lane saw the MMAs complete; otherwise rho keeps this unit's old
+    // entries and the timeout is reported by the next readout
+    if (!__all_sync(0xffffffffu, waited)) continue;
     fence_after_sync();
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {

@@ -91,7 +91,10 @@ struct tq_server {
   long long max_spin = 20000000;
   size_t rho_budget = 0, tab_budget = 0;
   DevBuf rho_mem, tab_mem, djobs, dblks, ditems, counters, ctl, results;
-  PinBuf pin;
+  // pinned staging, one buffer per use so that nothing in a tick waits for
+  // the tick's own copies: admission blobs, tick tables, readout results
+  // (all free again once the previous tick has been collected)
+  PinBuf pin, pin_tick, pin_res;
   Arena rho_arena, tab_arena;
   std::unordered_map<int, Req> reqs;
   std::deque<int> queue;
@@ -152,20 +155,29 @@ int quantum(int n) {
   return (int)std::min<long long>(1 << 20, 8ll << std::min(shift, 24));
 }
 
+// Layout of a request's table allocation: the uploaded blob, the per-op
+// superoperators, the fused FP64 superoperators and (split) their FP32
+// copies. Sets r.o_sops, r.o_sb and r.tab_bytes; returns the FP64 fused
+// table's offset.
+size_t table_layout(int prec, Req& r) {
+  size_t off = align_up(r.prog.blob_bytes, 256);
+  r.o_sops = off;
+  off = align_up(off + r.t.sop_entries * sizeof(double2), 256);
+  const size_t o_sb64 = off;
+  off = align_up(off + r.t.sb_entries * sizeof(double2), 256);
+  r.o_sb = prec == TQ_FP64 ? o_sb64 : off;
+  if (prec == TQ_SPLIT) off = align_up(off + r.t.sb_entries * sizeof(float2), 256);
+  r.tab_bytes = off;
+  return o_sb64;
+}
+
 // Admit the request: allocate, upload its tables, build + fuse, reset rho.
 tq_status admit(tq_server* s, Req& r, char* stage, size_t* stage_used) {
   const size_t esz = entry_size(s->prec);
   r.rho_bytes = esz << (2 * r.n);
   if (!s->rho_arena.alloc(r.rho_bytes, &r.rho_off)) return TQ_ERR_OOM;
   const tq_program& P = r.prog;
-  size_t off = align_up(P.blob_bytes, 256);
-  r.o_sops = off;
-  off = align_up(off + r.t.sop_entries * sizeof(double2), 256);
-  const size_t o_sb64 = off;
-  off = align_up(off + r.t.sb_entries * sizeof(double2), 256);
-  r.o_sb = s->prec == TQ_FP64 ? o_sb64 : off;
-  if (s->prec == TQ_SPLIT) off = align_up(off + r.t.sb_entries * sizeof(float2), 256);
-  r.tab_bytes = off;
+  const size_t o_sb64 = table_layout(s->prec, r);
   if (!s->tab_arena.alloc(r.tab_bytes, &r.tab_off)) {
     s->rho_arena.release(r.rho_off, r.rho_bytes);
     return TQ_ERR_OOM;
@@ -268,6 +280,10 @@ tq_status tq_server_submit(tq_server* s, int n_qubits, const tq_op* ops, size_t 
     if (st == TQ_OK && r.prog.max_width > 2) st = TQ_ERR_UNSUPPORTED;
   }
   if (st != TQ_OK) return st;
+  // its tables must fit the table arena on their own, or it would block the
+  // FIFO head forever
+  table_layout(s->prec, r);
+  if (align_up(r.tab_bytes, 256) > s->tab_budget) return TQ_ERR_OOM;
   for (int m = 0; m < n_masks; ++m) r.masks.push_back(masks[m]);
   const int id = s->next_id++;
   s->reqs.emplace(id, std::move(r));
@@ -290,7 +306,7 @@ tq_status collect_tick(tq_server* s, int* n_finished) {
   if (e != cudaSuccess) return st_of(e);
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, s->ev0, s->ev1) == cudaSuccess) s->gpu_ms += ms;
-  const char* h = static_cast<const char*>(s->pin.ptr);
+  const char* h = static_cast<const char*>(s->pin_res.ptr);
   int err_flag = 0;
   if (s->pend_items) std::memcpy(&err_flag, h + s->err_off, sizeof(int));
   if (!s->pend_done.empty()) {
@@ -310,11 +326,10 @@ tq_status collect_tick(tq_server* s, int* n_finished) {
   return err_flag ? TQ_ERR_TIMEOUT : TQ_OK;
 }
 
-// Admit and launch one tick without waiting for it (the previous tick must
-// have been collected).
+// Admit and launch one tick without waiting for it. The previous tick must
+// have been collected (which waited for the stream), so every staging buffer
+// is free; each is written once per tick, so no step below waits for the GPU.
 tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
-  cudaError_t e0 = cudaStreamSynchronize(s->stream);  // the staging buffer is reused below
-  if (e0 != cudaSuccess) return st_of(e0);
   cudaEventRecord(s->ev0, s->stream);
   // 1. admission, FIFO by HBM footprint: stop at the first request that does not fit
   size_t stage_need = 0;
@@ -394,11 +409,9 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
     if (e == cudaSuccess) e = grow_dev(s->ditems, bi);
     if (e == cudaSuccess) e = grow_dev(s->counters, jobs.size() * sizeof(int));
     if (e == cudaSuccess) e = grow_dev(s->ctl, 256);
-    // the admission uploads may still read the staging buffer: wait before reuse
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) e = grow_pin(s->pin, bj + bb + bi + 1024);
+    if (e == cudaSuccess) e = grow_pin(s->pin_tick, bj + bb + bi + 1024);
     if (e != cudaSuccess) return st_of(e);
-    char* h = static_cast<char*>(s->pin.ptr);
+    char* h = static_cast<char*>(s->pin_tick.ptr);
     std::memcpy(h, jobs.data(), bj);
     std::memcpy(h + align_up(bj, 256), blks.data(), bb);
     std::memcpy(h + align_up(bj, 256) + align_up(bb, 256), items.data(), bi);
@@ -439,10 +452,9 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
   }
   const size_t bj = done_jobs.size() * sizeof(BJob);
   const size_t br = done_jobs.size() * kResults * sizeof(double);
-  e = cudaStreamSynchronize(s->stream);  // staging reuse
-  if (e == cudaSuccess) e = grow_pin(s->pin, align_up(bj, 256) + br + 256);
+  e = grow_pin(s->pin_res, align_up(bj, 256) + br + 256);
   if (e != cudaSuccess) return st_of(e);
-  char* h = static_cast<char*>(s->pin.ptr);
+  char* h = static_cast<char*>(s->pin_res.ptr);
   s->res_off = align_up(bj, 256);
   s->err_off = s->res_off + br;
   if (!done_jobs.empty()) {
@@ -531,7 +543,8 @@ void tq_server_free(tq_server* s) {
   cudaStreamSynchronize(s->stream);
   for (DevBuf* d : {&s->rho_mem, &s->tab_mem, &s->djobs, &s->dblks, &s->ditems, &s->counters, &s->ctl, &s->results})
     if (d->ptr) cudaFree(d->ptr);
-  if (s->pin.ptr) cudaFreeHost(s->pin.ptr);
+  for (PinBuf* b : {&s->pin, &s->pin_tick, &s->pin_res})
+    if (b->ptr) cudaFreeHost(b->ptr);
   for (cudaEvent_t ev : {s->ev0, s->ev1})
     if (ev) cudaEventDestroy(ev);
   delete s;

@@ -1,6 +1,5 @@
 // tcgen05 building blocks of the split-precision width-2 pass on the tensor
-// cores (sm_103a), shared by the single-state kernel (tq_apply_tc.cu) and
-// the batch/serving kernel (tq_batch_kernels.cuh).
+// cores (sm_103a), used by the single-state kernel (tq_apply_tc.cu).
 //
 // The product y = S x of a width-2 block is a dense 16 x 16 complex
 // matrix-vector product per group (TANQ-Sim Sec. 3.1, the C2 update; its

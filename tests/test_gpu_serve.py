@@ -10,6 +10,8 @@ from paper_2404_13184_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
+SPLIT_Z = 1e-5              # stated split-precision bound on <Z> (trace-renormalised)
+SPLIT_TRACE_DRIFT = 1e-5    # stated bound on |Tr rho - 1| before renormalisation
 
 
 def _requests(count, seed, n_lo=2, n_hi=9):
@@ -56,12 +58,15 @@ def test_served_results_same_alone_and_in_mix(tq, precision):
     for k, (n, ops, masks) in enumerate(reqs):
         alone = _single(tq, precision, n, ops, masks)
         got = done[k].copy()
+        want = O.run_circuit(n, ops)
         if precision == "split":
-            got[2:] = got[2:]                         # both already renormalised by the trace
+            # <Z> of both split paths is already divided by the trace
             assert np.max(np.abs(got - alone)) < 1e-6
+            assert abs(got[0] - O.trace(want).real) < SPLIT_TRACE_DRIFT
+            for i, m in enumerate(masks):
+                assert abs(got[2 + i] - O.expect_z(want, m)) < SPLIT_Z, (k, i)
         else:
             assert np.array_equal(got, alone), k
-            want = O.run_circuit(n, ops)
             assert abs(got[0] - O.trace(want).real) < TOL64
             for i, m in enumerate(masks):
                 assert abs(got[2 + i] - O.expect_z(want, m)) < TOL64
@@ -147,4 +152,25 @@ def test_long_requests_stay_live_across_ticks(tq):
     with tq.State(12, "fp64") as st:
         st.run(long_c.ops, width=2)
         assert abs(res[2] - st.expect_z([1])[0]) < TOL64   # readouts reduce in a different order
+    srv.free()
+
+
+def test_submit_rejects_tables_beyond_the_table_budget(tq):
+    # a request whose superoperator tables can never fit the table arena is
+    # refused at submit (it would otherwise block the FIFO head for good);
+    # smaller requests queued behind the refused one still run
+    srv = tq.Server("fp64", rho_budget=64 << 20, table_budget=256 << 10, max_live=4)
+    big = W.random_noisy_circuit(6, 400, 31)       # > 100 fused 4 KiB superoperators alone
+    with pytest.raises(tq.TqError) as e:
+        srv.submit(6, big.ops, width=2, masks=[1])
+    assert e.value.status == 3                          # TQ_ERR_OOM
+    small = W.random_noisy_circuit(4, 5, 32)     # tables of a few superoperators: well below 256 KiB
+    rid = srv.submit(4, small.ops, width=2, masks=[1])
+    guard = 0
+    while srv.poll(rid)[0] != 2 and guard < 100:
+        srv.step()
+        guard += 1
+    st, res = srv.poll(rid)
+    want = O.run_circuit(4, small.ops)
+    assert st == 2 and abs(res[2] - O.expect_z(want, 1)) < TOL64
     srv.free()

@@ -36,6 +36,29 @@ def test_noalloc_readout_matches_expect_z_on_two_calls(tq, precision):
             assert np.max(np.abs(got - want)) < TOL[precision]
 
 
+@pytest.mark.parametrize("n,precision", [(14, "fp64"), (15, "split")])
+def test_noalloc_readout_multi_cta_partials(tq, n, precision):
+    # 14 and 15 qubits: the reduction runs on 32 and 64 CTAs, so the fixed
+    # scratch array holds many per-CTA partials; two calls in a row
+    import torch
+    c = W.random_noisy_circuit(4, 40, 11, gate_set=("h", "rx", "rz", "cx", "su2"))
+    masks_a = [0b11, 1, 1 << (n - 1), (1 << n) - 1]
+    masks_b = [1 << q for q in range(4)] + [0b1010, 0]
+    stream = torch.cuda.current_stream().cuda_stream
+    with tq.State(n, precision) as st:
+        for q in range(4, n):
+            st.run([("h", [q], ())], width=1)
+        for masks in (masks_a, masks_b):
+            st.run(c.ops, width=2)
+            want = st.expect_z(masks)
+            m = torch.tensor(masks, dtype=torch.int64, device="cuda")
+            out = torch.full((len(masks),), float("nan"), dtype=torch.float64, device="cuda")
+            tq.expect_z_noalloc(st.device_ptr(), n, precision, m.data_ptr(), len(masks), out.data_ptr(), stream)
+            got = out.cpu().numpy()
+            assert np.all(np.isfinite(got))
+            assert np.max(np.abs(got - want)) < TOL[precision]
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(tq):
     import torch
     with tq.State(4, "fp64") as st:
