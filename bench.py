@@ -62,10 +62,51 @@ def peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-def fp64_peak_tflops(sm_mhz: float) -> float:
-    # GB300 FP64 (DFMA) rate: 1.25 TFLOP/s nominal at 2070 MHz on 152 SMs,
-    # i.e. 4 FP64 flops (2 DFMA) per SM per clock.
-    return 152 * 4 * sm_mhz * 1e6 / 1e12
+def device_sms() -> int:
+    """Multiprocessor count of the current device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp64_peak_tflops(sm_mhz: float, sms: int | None = None) -> float:
+    """Nominal FP64 (DFMA) rate from unit counts and clock: 4 FP64 flops (2
+    DFMA) per SM per clock (1.26 TFLOP/s on 152 SMs at 2070 MHz)."""
+    return (sms or device_sms()) * 4 * sm_mhz * 1e6 / 1e12
+
+
+_PIPE_CACHE = {}
+
+
+def measured_pipe(tq, pipe: str) -> float:
+    """Measured rate of an arithmetic pipe (tq_pipe_rate), in TFLOP/s (FMA and
+    MMA pipes) or T ops/s (conversions); measured once per process."""
+    iters = {"dfma": 2048, "dmma": 512, "ffma": 65536, "cvt_f64_s64": 8192, "cvt_f64_f32": 8192}[pipe]
+    if pipe not in _PIPE_CACHE:
+        rate, _ = tq.pipe_rate(pipe, iters)
+        _PIPE_CACHE[pipe] = rate / 1e12
+    return _PIPE_CACHE[pipe]
+
+
+def host_cpu() -> dict:
+    """Threads available to this process and the CPU model of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            model = "unknown"
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def kernel_source_sha(symbol: str):
@@ -303,21 +344,44 @@ def oracle_prefix_time(n, ops, budget_s, min_ops=3):
     return done, time.perf_counter() - t0
 
 
-def cpu_baseline_circuits(circuits, budget_per_n=1.5):
-    """Oracle time of a set of circuits, estimated from a bounded sample: per
-    register size n, the first ops of the first circuit of that size run
-    until `budget_per_n` seconds (or the circuit ends) give the oracle's time
-    per op at n; the estimate is that time x the ops of every circuit of
-    size n. Returns (estimated seconds for all circuits, sample text)."""
-    per_op, parts = {}, []
+def cpu_baseline_circuits(circuits, budget_per_n=1.5, masks=(1, 3), full_max_n=6, full_count=8):
+    """Oracle time of a set of circuits, estimated from a bounded sample.
+    First the first `full_count` circuits of at most `full_max_n` qubits run
+    whole (their trace and <Z_mask> are kept, so the GPU results of those
+    circuits can be held to the oracle). Then per remaining register size n,
+    the first ops of the first circuit of that size run until
+    `budget_per_n` seconds (or the circuit ends). The estimate is the
+    oracle's time per op at each n x the ops of every circuit of size n.
+    Returns (estimated seconds for all circuits, sample text, {circuit index:
+    [Re tr, Im tr, <Z_m>...]})."""
+    import numpy as np
+    from oracle import dm_oracle
+    per_op, parts, full = {}, [], {}
+    spent = {}
+    for idx, c in enumerate(circuits):
+        if len(full) >= full_count:
+            break
+        if c.n > full_max_n:
+            continue
+        t0 = time.perf_counter()
+        rho = dm_oracle.run_circuit(c.n, c.ops)
+        dt = time.perf_counter() - t0
+        tr = complex(np.trace(rho))
+        full[idx] = [tr.real, tr.imag] + [float(dm_oracle.expect_z(rho, m)) for m in masks]
+        t, k = spent.get(c.n, (0.0, 0))
+        spent[c.n] = (t + dt, k + len(c.ops))
+    for n, (t, k) in spent.items():
+        per_op[n] = t / k
+    if full:
+        parts.append(f"{len(full)} whole circuits of <= {full_max_n} qubits")
     for c in circuits:
         if c.n not in per_op:
             done, dt = oracle_prefix_time(c.n, c.ops, budget_per_n)
             per_op[c.n] = dt / done
             parts.append(f"{done} ops at n={c.n}")
     total = sum(per_op[c.n] * len(c.ops) for c in circuits)
-    return total, ("oracle time per op measured per register size on a prefix of one circuit (" + ", ".join(parts)
-                   + "), times the ops of every circuit")
+    return total, ("oracle time per op measured per register size (" + ", ".join(parts)
+                   + "), times the ops of every circuit"), full
 
 
 def split_accuracy(tq, n=8, steps=30):
@@ -353,7 +417,7 @@ def autotune_cache():
 
 
 def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11, reference=None,
-              with_cpu=False):
+              with_cpu=False, oracle_results=None):
     """Batched sweep: `count` independent noisy circuits (n ~ U{4..11}, depth
     ~ U{50..500}, {H, RZ, RX, CX}, per-circuit depolarising p) in one
     persistent launch per run (a CUDA graph replay), tile and fusion width per
@@ -400,9 +464,16 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11
     hbm_gbs, sm_max, src = peaks()
     if precision == "fp64":
         ach = work["flops"] / (ms / 1e3) / 1e12
-        peak = fp64_peak_tflops(sm_max)
+        sms = device_sms()
+        peak = fp64_peak_tflops(sm_max, sms)
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "flops_per_run": work["flops"], "peak_source": "DFMA pipe: 152 SMs x 4 FP64 flop/clk x SM max clock"}
+                "flops_per_run": work["flops"],
+                "peak_source": f"DFMA pipe, nominal: {sms} SMs x 4 FP64 flop/clk x {sm_max:.0f} MHz"}
+        try:
+            meas = measured_pipe(tq, "dfma")
+            roof.update({"peak_measured_dfma": meas, "frac_of_measured_dfma": ach / meas})
+        except Exception:
+            pass
     else:
         ach = work["bytes"] / (ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
@@ -410,16 +481,25 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11
     gates = sum(c.n_gates for c in circuits)
     cpu = None
     if with_cpu:
-        est, sample = cpu_baseline_circuits(circuits)
-        cpu = {"value": count / est, "unit": "circuits/s", "cores": 1, "kind": "oracle", "sample": sample}
+        est, sample, oracle_results = cpu_baseline_circuits(circuits)
+        cpu = {"value": count / est, "unit": "circuits/s", "cores": 1, **host_cpu(), "kind": "oracle",
+               "sample": sample}
+    if oracle_results:
+        # the oracle's whole-circuit sample from the CPU-baseline leg: trace and
+        # <Z> of those circuits against the oracle
+        err["oracle_sample_circuits"] = len(oracle_results)
+        err["max_abs_z_err_vs_oracle_sample"] = max(max(abs(results[i][2] - o[2]), abs(results[i][3] - o[3]))
+                                                    for i, o in oracle_results.items())
+        err["max_abs_trace_err_vs_oracle_sample"] = max(abs(results[i][0] - o[0]) for i, o in oracle_results.items())
     return {"ms_per_run": ms, "circuits_per_s": count / (ms / 1e3), "gates_per_s": gates / (ms / 1e3),
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "oracle_results": oracle_results,
             "circuits": count, "noisy_gates": gates, "items": info["items"], "rho_bytes": info["rho_bytes"],
             "autotune": {str(n): {"tile_log2": t, "width": w, "ms": round(m, 3)} for n, (t, w, m) in tuned.items()},
             "autotune_s": t_tune, "accuracy": err, "roofline": roof, "results": results}
 
 
-def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=150 << 30, max_live=64):
+def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=150 << 30, max_live=64,
+              keep_small=0):
     """Poisson arrivals (`rate` per second for `duration` s) of random noisy
     circuits (n ~ U{5..15}, depth ~ U{50..2000}, 30% CX, depolarising and
     amplitude damping per request) served by the continuous-batching loop.
@@ -429,7 +509,10 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
     tick that collects its result. Ticks are pipelined (tq_server_step_async):
     the client's work overlaps the GPU, and gpu_busy_frac is the GPU time of
     the ticks (CUDA events) over the wall time. Requests unfinished when the
-    drain window ends are censored."""
+    drain window ends are censored. The returned dict carries, under
+    "_completed", the (n, depth) of every completed request and, for the
+    first `keep_small` completed requests of at most 6 qubits, their ops and
+    results under "_small" (both popped before printing)."""
     import numpy as np
     from paper_2404_13184_gb300 import workloads
     arrivals = workloads.poisson_arrivals(rate, duration, seed)
@@ -437,8 +520,8 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
     srv = tq.Server(precision, rho_budget=rho_budget, table_budget=8 << 30, max_live=max_live)
     t0 = time.perf_counter()
     nxt = 0
-    inflight = {}            # rid -> (arrival time, n, depth)
-    lat, done_n = [], []
+    inflight = {}            # rid -> (arrival time, n, depth, ops or None)
+    lat, done_n, completed, small = [], [], [], []
     queued_in_server = 0
     while True:
         now = time.perf_counter() - t0
@@ -449,7 +532,7 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
         if nxt < len(arrivals) and arrivals[nxt] <= now and queued_in_server < 8:
             c = workloads.served_request(rng)
             rid = srv.submit(c.n, c.ops, width=2, masks=[1])
-            inflight[rid] = (arrivals[nxt], c.n, c.n_gates)
+            inflight[rid] = (arrivals[nxt], c.n, c.n_gates, c.ops if c.n <= 6 else None)
             nxt += 1
             queued_in_server += 1
         if not inflight:
@@ -463,14 +546,17 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
         if fin:
             tdone = time.perf_counter() - t0
             for rid in list(inflight):
-                st, _ = srv.poll(rid)
+                st, res = srv.poll(rid)
                 if st == 2:
-                    arr, n, d = inflight.pop(rid)
+                    arr, n, d, ops = inflight.pop(rid)
                     lat.append(tdone - arr)
                     done_n.append(n)
+                    completed.append((n, d))
+                    if ops is not None and len(small) < keep_small:
+                        small.append((n, ops, [float(v) for v in res]))
     wall = time.perf_counter() - t0
     end = wall
-    censored = [end - a for a, _, _ in inflight.values()] + [end - a for a in arrivals[nxt:] if a <= end]
+    censored = [end - a for a, _, _, _ in inflight.values()] + [end - a for a in arrivals[nxt:] if a <= end]
     info = srv.info()
     busy = srv.gpu_ms() / 1e3      # GPU time of the collected ticks (CUDA events)
     srv.free()
@@ -479,13 +565,76 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
     def pct(v, q):
         return v[min(len(v) - 1, int(q * len(v)))] if v else None
     return {"precision": precision, "rate_per_s": rate, "arrival_window_s": duration, "drain_s": drain,
-            "arrived": sum(1 for a in arrivals if a <= end), "completed": len(lat),
+            "arrived": sum(1 for a in arrivals if a <= end), "completed": len(lat), "wall_s": wall,
             "circuits_per_s": len(lat) / wall, "p50_latency_s": pct(lat_sorted, 0.5),
             "p99_latency_s": pct(lat_sorted, 0.99), "censored": len(censored),
             "censored_min_latency_s": min(censored) if censored else None,
             "completed_qubit_counts": {str(k): done_n.count(k) for k in sorted(set(done_n))},
             "gpu_busy_frac": busy / wall, "ticks": info["ticks"], "blocks_applied": info["blocks_applied"],
-            "sustainable_rate_per_s": len(lat) / max(busy, 1e-9)}
+            "sustainable_rate_per_s": len(lat) / max(busy, 1e-9), "_completed": completed, "_small": small}
+
+
+def gate_slices(ops):
+    """Split a served request's ops into per-gate lists (a gate and the
+    channels attached after it)."""
+    out = []
+    for op in ops:
+        if op[0] in ("depol", "ad", "pd", "thermal") and out:
+            out[-1].append(op)
+        else:
+            out.append([op])
+    return out
+
+
+def plain_fp64_ms_per_gate(tq, torch, seed=SEED_SERVE, n_range=(5, 15), budget_s=2.0):
+    """The plain FP64 path (tq_run_circuit with no fusion: every gate and
+    every channel its own pass) on the served request distribution: per
+    register size n, the first request of that size in the stream's own
+    request sequence runs from |0><0|. Its first 10 gates (with their
+    channels) run as one tq_run_circuit call plus a synchronising <Z_0>
+    readout to estimate the rate; the next G gates, G chosen to take about
+    `budget_s` seconds (at most the rest of the request), run the same way
+    and are timed. Returns {n: (ms per noisy gate, gates timed)}: a request's
+    plain time is its depth x that rate (each gate's cost depends only on
+    its kind and n, and the kinds are drawn i.i.d.)."""
+    import numpy as np
+    from paper_2404_13184_gb300 import workloads
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    first = {}
+    guard = 0
+    while len(first) < n_range[1] - n_range[0] + 1 and guard < 100000:
+        c = workloads.served_request(rng)
+        first.setdefault(c.n, c)
+        guard += 1
+    out = {}
+    for n in sorted(first):
+        gates = gate_slices(first[n].ops)
+        st = tq.State(n, "fp64")
+        t0 = time.perf_counter()
+        st.run([op for g in gates[:10] for op in g], width=0)
+        st.expect_z([1])
+        est = (time.perf_counter() - t0) / 10
+        G = int(max(10, min(len(gates) - 10, budget_s / max(est, 1e-9))))
+        ops = [op for g in gates[10:10 + G] for op in g]
+        prog = tq.Program(ops)
+        t0 = time.perf_counter()
+        st.run(prog, width=0)
+        st.expect_z([1])
+        dt = time.perf_counter() - t0
+        st.free()
+        out[n] = (dt * 1e3 / G, G)
+    torch.cuda.synchronize()
+    return out
+
+
+def served_vs_plain(serve: dict, plain: dict) -> dict:
+    """The plain FP64 path's time for exactly the requests the server
+    completed (depth x the measured ms per gate at their n), against the
+    served run's wall time."""
+    completed = serve["_completed"]
+    t_plain = sum(d * plain[n][0] / 1e3 for n, d in completed)
+    return {"plain_fp64_s_for_completed": t_plain, "plain_fp64_circuits_per_s": len(completed) / max(t_plain, 1e-9),
+            "speedup_vs_plain_fp64": t_plain / serve["wall_s"]}
 
 
 def run_plain6(tq, torch, steps, warmup, with_cpu=True):
@@ -540,7 +689,7 @@ def run_plain6(tq, torch, steps, warmup, with_cpu=True):
             reps += 1
         dt = (time.perf_counter() - t0) / reps
         out["cpu_baseline"] = {"value": c.n_gates / dt, "unit": "noisy gates/s", "ms_per_circuit": dt * 1e3,
-                               "cores": 1, "kind": "oracle", "sample": f"the whole circuit, {reps} runs"}
+                               "cores": 1, **host_cpu(), "kind": "oracle", "sample": f"the whole circuit, {reps} runs"}
     return out
 
 
@@ -574,7 +723,7 @@ def run_purify(tq, precision):
     return out
 
 
-def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12, with_cpu=False):
+def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12, with_cpu=False, cpu_budget_s=20.0):
     """Layered thermal-relaxation workload (n = 12: 2^24 entries, 2000 gates):
     time of the whole circuit per fusion width (0 = unfused plain path) and
     the max-abs difference of <Z_i> and sampled vec(rho) entries to the
@@ -608,13 +757,72 @@ def run_layered(tq, torch, precision, widths=(0, 1, 2, 3, 4), n=12, with_cpu=Fal
         out[w]["speedup_vs_unfused"] = base / out[w]["ms"]
     line = {"n_qubits": n, "noisy_gates": c.n_gates, "widths": out}
     if with_cpu:
-        done, dt = oracle_prefix_time(n, c.ops, 20.0)
+        done, dt = oracle_prefix_time(n, c.ops, cpu_budget_s)
         est = dt * len(c.ops) / done
         line["cpu_baseline"] = {"value": c.n_gates / est, "unit": "noisy gates/s", "ms_per_circuit": est * 1e3,
-                                "cores": 1, "kind": "oracle",
+                                "cores": 1, **host_cpu(), "kind": "oracle",
                                 "sample": f"first {done} of the circuit's {len(c.ops)} ops (gates and channels), "
                                           f"{dt:.1f} s, time scaled by {len(c.ops)}/{done}"}
     return line
+
+
+def extras(tq, torch, args, with_cpu):
+    """The other configurations, at their stated sizes, as objects of the
+    benchmark line: plain 6-qubit circuit (unfused FP64), layered 12-qubit
+    thermal circuit (fusion widths 0-4, FP64 and split), the 1024-circuit
+    sweep (FP64 and split) and the served Poisson stream (FP64 and split,
+    with its speedup over the plain FP64 path and latency below saturation)."""
+    import numpy as np
+    out = {}
+    out["plain6"] = run_plain6(tq, torch, max(args.steps, 20), args.warmup, with_cpu=with_cpu)
+    out["layered12"] = {"n_qubits": 12, "fp64": run_layered(tq, torch, "fp64", with_cpu=with_cpu, cpu_budget_s=10.0),
+                        "split": run_layered(tq, torch, "split")}
+    sw = {}
+    ref, oracle_results = None, None
+    for prec in ("fp64", "split"):
+        r = run_sweep(tq, torch, prec, 3, 1, reference=ref, with_cpu=with_cpu and prec == "fp64",
+                      oracle_results=oracle_results)
+        res = r.pop("results")
+        oracle_results = r.pop("oracle_results")
+        if prec == "fp64":
+            ref = res
+        sw[prec] = r
+    out["sweep"] = {"circuits": 1024, "n_qubits": "4-11", "depth": "50-500", **sw}
+    if args.serve_window > 0:
+        sv = {}
+        plain = plain_fp64_ms_per_gate(tq, torch)
+        for prec in ("fp64", "split"):
+            r = run_serve(tq, prec, args.serve_rate, args.serve_window, args.serve_drain_in_line,
+                          keep_small=6 if with_cpu else 0)
+            r.update(served_vs_plain(r, plain))
+            small = r.pop("_small")
+            r.pop("_completed")
+            if with_cpu and small:
+                # CPU-baseline leg: the oracle on a sample of the completed
+                # small requests, for correctness only
+                from oracle import dm_oracle
+                errz, errt = 0.0, 0.0
+                for n, ops, res in small:
+                    rho = dm_oracle.run_circuit(n, ops)
+                    errt = max(errt, abs(res[0] - float(np.trace(rho).real)))
+                    errz = max(errz, abs(res[2] - float(dm_oracle.expect_z(rho, 1))))
+                r["oracle_sample"] = {"requests": len(small), "max_abs_z_err": errz, "max_abs_trace_err": errt}
+            sv[prec] = r
+        sub = []
+        for prec in ("fp64", "split"):
+            cap = sv[prec]["sustainable_rate_per_s"]
+            for f in (0.5, 0.8):
+                r = run_serve(tq, prec, f * cap, 15.0, 15.0)
+                for k in ("_small", "_completed"):
+                    r.pop(k)
+                sub.append({"precision": prec, "fraction_of_sustainable": f, **{k: r[k] for k in (
+                    "rate_per_s", "arrived", "completed", "censored", "p50_latency_s", "p99_latency_s",
+                    "circuits_per_s", "gpu_busy_frac")}})
+        sv["sub_saturation"] = sub
+        sv["plain_fp64_ms_per_gate"] = {str(n): {"ms_per_gate": v[0], "gates_timed": v[1]} for n, v in plain.items()}
+        sv["speedup_vs_plain_fp64"] = {p_: sv[p_]["speedup_vs_plain_fp64"] for p_ in ("fp64", "split")}
+        out["serve"] = sv
+    return out
 
 
 def reference_arm(args, world, rank):
@@ -635,8 +843,8 @@ def reference_arm(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "tfim-ring-15q", "n_qubits": N_QUBITS},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                             "raw_value_at_sample_size": raw},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, **host_cpu(), "kind": "oracle",
+                             "sample": sample, "raw_value_at_sample_size": raw},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -663,8 +871,12 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-duration", type=float, default=60.0)
     ap.add_argument("--serve-drain", type=float, default=60.0)
-    ap.add_argument("--serve-in-line", type=float, default=15.0,
-                    help="seconds of split-precision served stream added to the tfim15 line (0: none)")
+    ap.add_argument("--serve-window", type=float, default=60.0,
+                    help="arrival window (s) of the served streams added to the tfim15 line (0: none)")
+    ap.add_argument("--serve-drain-in-line", type=float, default=20.0,
+                    help="drain window (s) after the in-line served streams' arrivals stop")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="tfim15 line only: leave out the plain6, layered12, sweep and serve objects")
     args = ap.parse_args()
     global N_QUBITS
     N_QUBITS = args.n_qubits
@@ -720,6 +932,7 @@ def main():
                               reference=fp64_results if prec == "split" else None,
                               with_cpu=prec == precs[0] and rank == 0 and not args.no_cpu_baseline)
                 res = r.pop("results")
+                r.pop("oracle_results")
                 if prec == "fp64":
                     fp64_results = res
                 line = {"metric": "batched sweep circuits/s",
@@ -727,6 +940,8 @@ def main():
                         "dtype": "f64" if prec == "fp64" else "f32", **r}
             else:
                 r = run_serve(tq, prec, args.serve_rate, args.serve_duration, args.serve_drain)
+                for k in ("_small", "_completed"):
+                    r.pop(k)
                 line = {"metric": "served circuits/s + p99 latency", "workload": "poisson-served (n 5-15, depth "
                         "50-2000)", "dtype": "f64" if prec == "fp64" else "f32", **r}
             if rank == 0:
@@ -745,14 +960,19 @@ def main():
     clk = fp64["clocks"] or {}
     sm_mhz = clk.get("sm_mhz") or sm_max_cfg
     name64, st64 = dominant(fp64["stats"])
+    sms = device_sms()
     ach64 = st64["flops"] * st64["launches"] / (st64["total_ms"] / 1e3) / 1e12
-    peak64 = fp64_peak_tflops(sm_max_cfg)
+    pipes = {p_: measured_pipe(tq, p_) for p_ in ("dfma", "dmma", "ffma", "cvt_f64_s64", "cvt_f64_f32")}
+    peak64 = fp64_peak_tflops(sm_max_cfg, sms)
     roof = {"kernel": name64, "bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
             "frac": ach64 / peak64, "traffic": traffic_from_profile(name64),
             "algorithmic_bytes_per_launch": st64["bytes"], "algorithmic_flops_per_launch": st64["flops"],
+            "flops_count": "8 per nonzero of the row lists the kernel applied (read back from the device), per "
+                           "canonical group" if "sparse" in name64 else "dense 8 x 16^w per canonical group",
             "launches": st64["launches"], "avg_launch_ms": st64["total_ms"] / st64["launches"],
-            "peak_source": "DFMA pipe: 152 SMs x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
-            "frac_at_measured_clock": ach64 / fp64_peak_tflops(sm_mhz)}
+            "peak_source": f"DFMA pipe, nominal: {sms} SMs x 4 FP64 flop/clk x {sm_max_cfg:.0f} MHz",
+            "frac_at_measured_clock": ach64 / fp64_peak_tflops(sm_mhz, sms),
+            "peak_measured_dfma": pipes["dfma"], "frac_of_measured_dfma": ach64 / pipes["dfma"]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K64, "warmup": W,
             "ms_per_step": ms64 / K64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -766,6 +986,10 @@ def main():
                        "l2": "inputs larger than L2 (16 GiB rho), no flush", "parallelism": "replicas"
                        if world > 1 else "single"},
             "roofline": roof, "gpu_launches": fp64["launches"],
+            "pipes_measured": {"dfma_tflops": pipes["dfma"], "dmma_tflops": pipes["dmma"], "ffma_tflops": pipes["ffma"],
+                               "cvt_f64_s64_tops": pipes["cvt_f64_s64"], "cvt_f64_f32_tops": pipes["cvt_f64_f32"],
+                               "how": "tq_pipe_rate: 8 independent chains per thread, 4 x 256 threads per SM on "
+                                      "every SM, best of 3 launches (CUDA events)"},
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons", []), "samples": clk.get("samples")},
             "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)}
@@ -792,11 +1016,12 @@ def main():
                                       "avg_launch_ms": ss["total_ms"] / ss["launches"],
                                       "peak_source": f"{peak_src} HBM copy bandwidth"},
                          "gpu_launches": split["launches"]}
-    if args.serve_in_line > 0 and not args.no_split:
-        line["serve"] = run_serve(tq, "split", args.serve_rate, args.serve_in_line, args.serve_in_line)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if world == 1 and not args.no_extras:
+        line.update(extras(tq, torch, args, with_cpu))
+    if with_cpu:
         scaled, raw, dt = cpu_sample_rate(2)
-        line["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": scaled, "unit": UNIT, "cores": 1, **host_cpu(), "kind": "oracle",
                                 "sample": f"2 x (RZZ+2q depolarising, RX+1q depolarising) of the ring TFIM on a "
                                           f"{SAMPLE_QUBITS}-qubit register ({dt:.1f} s, {raw:.3g} gates/s), scaled by "
                                           f"4^-{N_QUBITS - SAMPLE_QUBITS} to 15 qubits (oracle cost per op ~ 4^n)"}

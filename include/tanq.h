@@ -436,14 +436,42 @@ tq_status tq_expect_z_noalloc(const void* rho_dev, int n_qubits, int precision,
                               const uint64_t* masks_dev, int n_masks, double* out_dev,
                               void* cuda_stream);
 
+/* ---- pipe-rate probes (roofline denominators) ---------------------------
+ * The paper has no counterpart; these measure the issue rates the apply
+ * kernels' rooflines are taken against, where a copy benchmark or a cuBLAS
+ * GEMM gives none: the FP64 FMA pipe (the FP64 apply passes are bound by
+ * it), the FP64 tensor path (mma.sync m8n8k4, the paper's Sec. 3.2 mapping),
+ * FP32 FMA, and two conversions to FP64. */
+typedef enum {
+  TQ_PIPE_DFMA = 0,        /* fma.rn.f64: 2 flops per FMA */
+  TQ_PIPE_DMMA = 1,        /* mma.sync.m8n8k4.f64: 512 flops per warp instruction */
+  TQ_PIPE_FFMA = 2,        /* fma.rn.f32: 2 flops per FMA */
+  TQ_PIPE_CVT_F64_S64 = 3, /* cvt.rn.f64.s64: 1 op per conversion */
+  TQ_PIPE_CVT_F64_F32 = 4  /* cvt.f64.f32: 1 op per conversion */
+} tq_pipe;
+
+/* Run the probe of `pipe` on every SM of the current device (4 CTAs of 256
+ * threads per SM, 8 independent chains per thread, `iters` x 16 instructions
+ * per chain; 1 <= iters <= 2^24), four launches on a private stream, and
+ * return the best of the last three as *ops_per_s (flops/s for the FMA and
+ * MMA pipes, conversions/s otherwise) and its duration *ms (may be NULL).
+ * Synchronous; allocates 256 bytes of device memory for the call. */
+tq_status tq_pipe_rate(int pipe, int iters, double* ops_per_s, double* ms);
+
 /* ---- per-launch profiling (CUDA events on the state's stream) ---------- */
 
 typedef struct tq_kernel_stat {
   char name[32];      /* e.g. "apply_f64_w2", "superop_build", "fuse", "reduce" */
   uint64_t launches;
   double total_ms;    /* sum of event-timed launch durations */
-  double flops;       /* algorithmic flops per launch (dense superoperator count) */
-  double bytes;       /* algorithmic HBM bytes per launch (read + write of rho) */
+  double flops;       /* algorithmic flops per launch, averaged over the launches:
+                         8 per complex multiply-add of every computed group (Sec.
+                         3.1) -- the dense 16^w count, except for the row-list
+                         kernels ("apply_f64_sparse_w*"), which count the
+                         nonzeros of the row lists they applied, read back from
+                         the device after compression */
+  double bytes;       /* algorithmic HBM bytes per launch, averaged over the
+                         launches (one read + one write of every computed entry) */
 } tq_kernel_stat;
 
 /* Turn event timing of every kernel launch on (1) or off (0); turning it on

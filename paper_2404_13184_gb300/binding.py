@@ -100,6 +100,7 @@ _SIGNATURES = [
                                POINTER(ctypes.c_ulonglong)]),
     ("tq_server_free", None, [c_void_p]),
     ("tq_expect_z_noalloc", c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_void_p, c_void_p]),
+    ("tq_pipe_rate", c_int, [c_int, c_int, POINTER(c_double), POINTER(c_double)]),
     ("tq_profile_enable", c_int, [c_void_p, c_int]),
     ("tq_profile_read", c_int, [c_void_p, POINTER(TqKernelStat), c_int, POINTER(c_int)]),
     ("tq_launch_count", c_int, [c_void_p, POINTER(c_uint64)]),
@@ -387,6 +388,19 @@ def channel_kraus(name: str, k: int, params) -> list[np.ndarray]:
     _check(lib.tq_channel_kraus(CHANNELS[name], k, _dptr(p), m.value, ctypes.byref(m), _dptr(out)), "tq_channel_kraus")
     arr = out.view(np.complex128).reshape(m.value, d, d)
     return [arr[i] for i in range(m.value)]
+
+
+PIPES = {"dfma": 0, "dmma": 1, "ffma": 2, "cvt_f64_s64": 3, "cvt_f64_f32": 4}
+
+
+def pipe_rate(pipe: str, iters: int = 2048):
+    """Measured issue rate of an arithmetic pipe on the current device (see
+    tq_pipe_rate in include/tanq.h): (ops or flops per second, ms of the best
+    launch)."""
+    lib = load()
+    r, ms = c_double(0.0), c_double(0.0)
+    _check(lib.tq_pipe_rate(PIPES[pipe], iters, ctypes.byref(r), ctypes.byref(ms)), "tq_pipe_rate")
+    return r.value, ms.value
 
 
 def expect_z_noalloc(rho_dev_ptr: int, n: int, precision: str, masks_dev_ptr: int, n_masks: int,

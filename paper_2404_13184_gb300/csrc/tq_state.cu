@@ -33,6 +33,45 @@ struct Pending {
   cudaEvent_t e0, e1;
 };
 
+// Algorithmic flops of a row-list launch, resolved once the row lists it
+// applied have been copied back: 8 flops per applied nonzero per group.
+struct PendingFlops {
+  int kind;
+  double groups;
+  const int* rowptr;  // pinned host copy of the block's rowptr[0..16]
+  int dim;            // rowptr[dim] = nonzeros of the block
+};
+
+// Pinned host memory for the row-list counts of profiled launches, in chunks
+// that are never reallocated (pending copies keep pointing into them).
+struct CountArena {
+  static constexpr size_t kChunkInts = 1 << 14;
+  std::vector<int*> chunks;
+  size_t used = 0;  // ints used in the last chunk
+  int* take(size_t ints) {
+    if (ints > kChunkInts) return nullptr;
+    if (chunks.empty() || used + ints > kChunkInts) {
+      void* p = nullptr;
+      if (cudaHostAlloc(&p, kChunkInts * sizeof(int), cudaHostAllocDefault) != cudaSuccess) return nullptr;
+      chunks.push_back(static_cast<int*>(p));
+      used = 0;
+    }
+    int* out = chunks.back() + used;
+    used += ints;
+    return out;
+  }
+  void reset() {
+    for (size_t i = 1; i < chunks.size(); ++i) cudaFreeHost(chunks[i]);
+    if (chunks.size() > 1) chunks.resize(1);
+    used = 0;
+  }
+  void release() {
+    for (int* c : chunks) cudaFreeHost(c);
+    chunks.clear();
+    used = 0;
+  }
+};
+
 }  // namespace
 
 struct tq_state {
@@ -59,8 +98,10 @@ struct tq_state {
   std::vector<cudaEvent_t> event_pool;
   uint64_t prof_launches[K_NKINDS] = {};
   double prof_ms[K_NKINDS] = {};
-  double prof_flops[K_NKINDS] = {};
-  double prof_bytes[K_NKINDS] = {};
+  double prof_flops[K_NKINDS] = {};  // summed over launches
+  double prof_bytes[K_NKINDS] = {};  // summed over launches
+  std::vector<PendingFlops> pending_flops;
+  CountArena counts;
 };
 
 namespace {
@@ -171,6 +212,8 @@ cudaError_t timed(tq_state* s, int kind, int count, F launch) {
   return e;
 }
 
+// Fold finished launches into the statistics (the stream has been
+// synchronised, so the row-list counts have landed in host memory).
 void fold_pending(tq_state* s) {
   for (const Pending& pd : s->pending) {
     float ms = 0.f;
@@ -179,6 +222,9 @@ void fold_pending(tq_state* s) {
     s->event_pool.push_back(pd.e1);
   }
   s->pending.clear();
+  for (const PendingFlops& pf : s->pending_flops) s->prof_flops[pf.kind] += 8.0 * pf.groups * (double)pf.rowptr[pf.dim];
+  s->pending_flops.clear();
+  s->counts.reset();
 }
 
 // ---- planning ------------------------------------------------------------
@@ -378,6 +424,17 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
       return launch_compress_sparse(sb64, d_blk, reinterpret_cast<const SparseWork*>(d + P.o_spw), P.n_sparse, sps,
                                     s->stream);
     });
+  // profiling: copy every row list's rowptr back, so that the flops of a
+  // row-list launch count the nonzeros it actually applied
+  const int* counts = nullptr;
+  if (e == cudaSuccess && s->prof_on && P.n_sparse > 0) {
+    constexpr size_t kRow = sizeof(SparseBlock::rowptr);
+    int* h = s->counts.take((size_t)P.n_sparse * (kRow / sizeof(int)));
+    if (!h) return TQ_ERR_OOM;
+    e = cudaMemcpy2DAsync(h, kRow, sps, sizeof(SparseBlock), kRow, (size_t)P.n_sparse, cudaMemcpyDeviceToHost,
+                          s->stream);
+    counts = h;
+  }
   const double entries = (double)(1ull << (2 * s->n));
   const bool herm_state = s->herm_mode && s->herm_ok;
   for (size_t b = 0; b < P.params.size() && e == cudaSuccess; ++b) {
@@ -406,11 +463,12 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
     if (herm && s->prec == TQ_SPLIT && p.width == 2) s->tc_used = true;
     e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream, spb); });
     if (s->prof_on) {  // per launch: the groups computed x (8 * 16^w flops, 2 * B * 4^w bytes) each
-      const double per = (double)(1 << (2 * p.width));
-      // sparse blocks: the structural nonzeros (exact zeros are skipped, so
-      // the work done can only be smaller)
-      s->prof_flops[kind] = 8.0 * groups * (sparse ? (double)P.nnz[b] : per * per);
-      s->prof_bytes[kind] = 2.0 * groups * per * (double)entry_bytes(s->prec);
+      const int per = 1 << (2 * p.width);
+      if (sparse)  // 8 flops per nonzero of the row lists the kernel applied
+        s->pending_flops.push_back(PendingFlops{kind, groups, counts + (size_t)P.sp_slot[b] * 17, per});
+      else
+        s->prof_flops[kind] += 8.0 * groups * (double)per * (double)per;
+      s->prof_bytes[kind] += 2.0 * groups * (double)per * (double)entry_bytes(s->prec);
     }
     (void)entries;
   }
@@ -593,6 +651,7 @@ void tq_free(tq_state* s) {
     cudaEventDestroy(pd.e1);
   }
   for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
+  s->counts.release();
   delete s;
 }
 
@@ -997,6 +1056,7 @@ tq_status tq_profile_enable(tq_state* s, int on) {
   if (on) {
     cudaStreamSynchronize(s->stream);
     fold_pending(s);
+    s->counts.release();
     for (int k = 0; k < K_NKINDS; ++k) {
       s->prof_launches[k] = 0;
       s->prof_ms[k] = s->prof_flops[k] = s->prof_bytes[k] = 0.0;
@@ -1020,8 +1080,8 @@ tq_status tq_profile_read(tq_state* s, tq_kernel_stat* out, int capacity, int* c
       std::strncpy(o.name, kKindName[k], sizeof(o.name) - 1);
       o.launches = s->prof_launches[k];
       o.total_ms = s->prof_ms[k];
-      o.flops = s->prof_flops[k];
-      o.bytes = s->prof_bytes[k];
+      o.flops = s->prof_flops[k] / (double)s->prof_launches[k];
+      o.bytes = s->prof_bytes[k] / (double)s->prof_launches[k];
     }
     ++c;
   }

@@ -343,6 +343,29 @@ def test_profile_counts_launches(tq):
     for k, v in applies.items():
         assert v["bytes"] == 2 * 16 * groups * 16
         assert 0 < v["flops"] <= 8.0 * groups * 16 * 16
+
+
+def test_profile_counts_the_row_list_nonzeros_applied(tq):
+    # unfused single ops whose superoperators have closed-form nonzero counts
+    # (local index l = r + 2 c, S = conj(K) (x) K summed over the Kraus set):
+    #   1-qubit depolarising: S00,00 S00,11 S11,00 S11,11 and the two
+    #   coherences S01,01 S10,10 -> 6 of 16;
+    #   amplitude damping: S00,00 S00,11 S11,11 S01,01 S10,10 -> 5;
+    #   CX (a permutation of the 16 local entries): 16 of 256.
+    # The row-list kernels' flops per launch are 8 x (canonical groups) x
+    # those counts, read back from the device's row lists.
+    n = 7
+    cases = [([("depol", [2], (0.01,))], "apply_f64_sparse_w1", 1, 6),
+             ([("ad", [5], (0.2,))], "apply_f64_sparse_w1", 1, 5),
+             ([("cx", [1, 4], ())], "apply_f64_sparse_w2", 2, 16)]
+    for ops, kind, w, nnz in cases:
+        with tq.State(n, "fp64") as st:
+            st.profile(True)
+            st.run(ops, width=0)
+            stats = st.profile_stats()
+        M = 2 ** (n - w)
+        assert stats[kind]["launches"] == 1
+        assert stats[kind]["flops"] == 8.0 * (M * (M + 1) // 2) * nnz, (ops, stats[kind]["flops"])
     assert all(v["total_ms"] > 0 for v in stats.values())
 
 
