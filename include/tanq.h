@@ -175,6 +175,35 @@ tq_status tq_set_hermitian(tq_state* s, int on);
 /* *active = 1 if apply passes currently use Hermitian mode. */
 tq_status tq_is_hermitian_mode(const tq_state* s, int* active);
 
+/* Products of the FP64 apply passes (TQ_FP64 states).
+ *  TQ_ENGINE_DFMA    FP64 fused multiply-adds on the CUDA cores (dense
+ *                    kernels, or row lists of the nonzero superoperator
+ *                    entries for structured blocks).
+ *  TQ_ENGINE_TENSOR  blocks of width <= 2 in Hermitian mode on registers of
+ *                    n >= 6 qubits run on the tcgen05 tensor cores: every
+ *                    operand (the group's 32 real values, each real row of
+ *                    the superoperator) is cut into eight 7-bit digits of a
+ *                    56-bit fixed-point number aligned to the largest
+ *                    exponent of its group or row; the digit products, on
+ *                    BF16 tensor cores, are summed EXACTLY in FP32 per digit
+ *                    order (Ozaki-style error-free splitting) and recombined
+ *                    in 64-bit integers, so each output carries the error of
+ *                    one rounding plus the operands' rounding at 2^-57 of
+ *                    their alignment: FP64 accuracy relative to the largest
+ *                    entry of its group (the paper's FP64 tensor-core C2
+ *                    update, Sec. 3.2, mapped onto the tensor cores this GPU
+ *                    has). A width-1 block runs as S (x) I on two qubits.
+ *                    Other blocks use the DFMA kernels.
+ *  TQ_ENGINE_AUTO    the library's choice (the default).
+ * The engine is read when passes are enqueued (a device program's captured
+ * graph is recaptured when it changes). */
+typedef enum { TQ_ENGINE_AUTO = 0, TQ_ENGINE_DFMA = 1, TQ_ENGINE_TENSOR = 2 } tq_fp64_engine;
+tq_status tq_set_fp64_engine(tq_state* s, int engine);
+
+/* *on_tensor = 1 if the state's FP64 passes of widths <= 2 run on the tensor
+ * cores (TQ_ENGINE_TENSOR, or TQ_ENGINE_AUTO where the library chooses them). */
+tq_status tq_fp64_on_tensor(const tq_state* s, int* on_tensor);
+
 /* Copy vec(rho) out to / in from host memory: 2 * 4^n doubles, interleaved
  * (re, im) in vec order (index r + c 2^n). Split states convert from/to
  * complex64. tq_get_rho waits for the stream. */
@@ -203,8 +232,9 @@ tq_status tq_run_circuit(tq_state* s, const tq_op* ops, size_t n_ops, int max_fu
                          size_t* n_blocks_out);
 
 /* Failure-detection hook for tests (the paper has no counterpart): the
- * MMA-completion waits of the split tensor-core pass (width-2 blocks of a
- * TQ_SPLIT state in Hermitian mode) give up after max_tries try-wait rounds
+ * MMA-completion waits of the tensor-core passes (width-2 blocks of a
+ * TQ_SPLIT state in Hermitian mode, and the FP64 passes of
+ * TQ_ENGINE_TENSOR) give up after max_tries try-wait rounds
  * (0 restores the default, ~seconds); with skip_mma != 0 the passes
  * launched afterwards issue neither their MMAs nor the commit, so their
  * first wait runs out with nothing in flight and the next synchronising

@@ -58,6 +58,8 @@ _SIGNATURES = [
     ("tq_rho_device_ptr", c_int, [c_void_p, POINTER(c_void_p)]),
     ("tq_set_hermitian", c_int, [c_void_p, c_int]),
     ("tq_is_hermitian_mode", c_int, [c_void_p, POINTER(c_int)]),
+    ("tq_set_fp64_engine", c_int, [c_void_p, c_int]),
+    ("tq_fp64_on_tensor", c_int, [c_void_p, POINTER(c_int)]),
     ("tq_get_rho", c_int, [c_void_p, POINTER(c_double)]),
     ("tq_set_rho", c_int, [c_void_p, POINTER(c_double)]),
     ("tq_apply_gate", c_int, [c_void_p, POINTER(c_int), c_int, POINTER(c_double)]),
@@ -390,6 +392,7 @@ def channel_kraus(name: str, k: int, params) -> list[np.ndarray]:
     return [arr[i] for i in range(m.value)]
 
 
+ENGINES = {"auto": 0, "dfma": 1, "tensor": 2}
 PIPES = {"dfma": 0, "dmma": 1, "ffma": 2, "cvt_f64_s64": 3, "cvt_f64_f32": 4}
 
 
@@ -443,7 +446,7 @@ class State:
     """A density matrix on the GPU (tq_state)."""
 
     def __init__(self, n: int, precision: str = "fp64", stream=None, torch_memory: bool = True,
-                 hermitian: bool = True):
+                 hermitian: bool = True, engine: str | None = None):
         lib = load()
         self.n = n
         self.precision = precision
@@ -463,9 +466,20 @@ class State:
             _check(lib.tq_create(n, prec, c_void_p(stream), ctypes.byref(self._h)), "tq_create")
         if not hermitian:
             _check(lib.tq_set_hermitian(self._h, 0), "tq_set_hermitian")
+        if engine is not None:
+            self.set_fp64_engine(engine)
 
     def set_hermitian(self, on: bool):
         _check(_lib.tq_set_hermitian(self._h, 1 if on else 0), "tq_set_hermitian")
+
+    def set_fp64_engine(self, engine: str):
+        """'auto', 'dfma' or 'tensor' (tq_set_fp64_engine)."""
+        _check(_lib.tq_set_fp64_engine(self._h, ENGINES[engine]), "tq_set_fp64_engine")
+
+    def fp64_on_tensor(self) -> bool:
+        v = c_int(0)
+        _check(_lib.tq_fp64_on_tensor(self._h, ctypes.byref(v)), "tq_fp64_on_tensor")
+        return bool(v.value)
 
     def hermitian_mode(self) -> bool:
         v = c_int(0)
@@ -509,12 +523,12 @@ class State:
         _check(_lib.tq_profile_enable(self._h, 1 if on else 0), "tq_profile_enable")
 
     def profile_stats(self) -> dict:
-        arr = (TqKernelStat * 16)()
+        arr = (TqKernelStat * 32)()
         cnt = c_int(0)
-        _check(_lib.tq_profile_read(self._h, arr, 16, ctypes.byref(cnt)), "tq_profile_read")
+        _check(_lib.tq_profile_read(self._h, arr, 32, ctypes.byref(cnt)), "tq_profile_read")
         return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
                                        "flops": float(arr[i].flops), "bytes": float(arr[i].bytes)}
-                for i in range(min(cnt.value, 16))}
+                for i in range(min(cnt.value, 32))}
 
     def launch_count(self) -> int:
         v = c_uint64(0)

@@ -1,0 +1,434 @@
+// FP64-accurate width-2 apply pass on the 5th-generation tensor cores
+// (tcgen05, sm_103a), Hermitian mode, for single FP64 states: the product
+// y = S x of every canonical group (TANQ-Sim Sec. 3.1, the C2 update; the
+// paper maps it onto FP64 tensor cores in Sec. 3.2) computed from exact
+// integer products on the BF16 tensor cores, in the manner of the
+// Ozaki-Ogita-Oishi error-free splitting of a dot product.
+//
+// Real-ified product (as in tq_tc.cuh, without taking out the identity):
+// Y[m][n] = sum_k X[m][k] R[n][k], with m one of 128 groups, k one of the
+// 32 real inputs (Re, Im of the 16 entries, interleaved) and n one of the 32
+// real outputs.
+//
+// Fixed-point slicing. Every operand value is cut into eight 7-bit digits
+// of a 56-bit fixed-point number aligned to a shared exponent: for group m
+// the largest biased exponent E_m of its 32 values, for output row n of R
+// the largest biased exponent G_n of the row. With F the value's 53-bit
+// significand shifted to that alignment (rounded to nearest, 56 bits),
+//     |v| ~ F * 2^(E - 1078),  F = sum_i d_i 2^(49 - 7 i),  0 <= d_i < 128,
+// and the BF16 operand of digit i is +-d_i 2^(-7 i) (exact: 7 significant
+// bits). Then
+//     Y[m][n] ~ 2^(E_m + G_n - 2100 + 42) sum_t C_t,
+//     C_t = sum_{i + j = t} sum_k A_i[m][k] B_j[n][k] = 2^(-7 t) P_t,
+// P_t an integer with |P_t| <= (t + 1) * 32 * 127^2 < 2^22 for t <= 7: every
+// partial sum of an order is an integer multiple of 2^(-7 t) below 2^22 of
+// those units, so FP32 accumulation in tensor memory is EXACT for each
+// order. Orders 0..5 get an accumulator each; orders 6 and 7 (weight <=
+// 2^-42 of order 0) share one, whose FP32 roundings are ~2^-58 of the
+// largest term; orders >= 8 (~2^-53) are dropped.
+//
+// Recombination without FP64 arithmetic: each exact accumulator becomes its
+// integer by one FP32 add of 1.5 * 2^(23 - 7 t) (the float's low mantissa
+// bits then hold P_t); the shared accumulator is rounded to units of 2^-42
+// the same way. The integers are combined into one 64-bit integer Z (in
+// units of 2^-42 of C_0; |Z| < 2^62) with wide integer multiply-adds, Z is
+// converted to FP64 (one rounding) and scaled by adding E_m + G_n - 2100 to
+// its exponent field. Per real output that is one conversion and no FP64
+// multiply or add; the result is FP64-accurate relative to the group's
+// largest entry (rounding of the operands at 2^-57 of their alignment,
+// ~2^-53 from the dropped orders, one final rounding).
+//
+// Work unit, group walk and Hermitian bookkeeping follow the split
+// tensor-core kernel (tq_apply_tc.cu): half of a 16 x 16 tile of canonical
+// groups, one group per thread, a CTA of 128 threads. Per unit a thread
+// issues the loads of its next group's 16 entries into registers, slices the
+// current group into the eight digit operands (A_0..A_7, 8 KB each in shared
+// memory), and after a CTA barrier one thread issues the 72 MMAs (36 digit
+// pairs x two K-halves, M = 128, N = 32, K = 16) into 7 accumulators of 32
+// tensor-memory columns and commits them to an mbarrier; every thread waits
+// (bounded), reads its row of the accumulators and writes its 16 outputs.
+//
+// Width-1 blocks run through the same kernel as a width-2 block with the
+// identity on a second qubit (S (x) I, built while slicing R), which moves
+// the same number of bytes as a width-1 Hermitian pass.
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
+#include "tq_device.cuh"
+#include "tanq.h"
+#include "tq_tc.cuh"
+
+namespace tq {
+
+namespace {
+
+using namespace tc;
+
+// MMA-completion waits of this kernel that gave up; read and cleared by
+// oz_take_timeouts().
+__device__ unsigned int g_oz_timeouts;
+
+constexpr int kThreads = 128;
+constexpr int kTile = 16;
+constexpr int kDigits = 8;                          // 7-bit digits per operand value
+constexpr int kAccs = 7;                            // orders 0..5 exact, 6 and 7 shared
+constexpr uint32_t kADigitBytes = 128 * kRowBytes;  // 128 groups x 32 BF16
+constexpr uint32_t kOffA = 0;
+constexpr uint32_t kOffB = kOffA + kDigits * kADigitBytes;
+constexpr uint32_t kOffG = kOffB + kDigits * kBTermBytes;  // 32 row exponents
+constexpr uint32_t kOffBar = kOffG + 32 * 4;
+constexpr uint32_t kOffTmem = kOffBar + 8;
+constexpr uint32_t kOffFlag = kOffTmem + 4;
+constexpr uint32_t kSmemBytes = kOffFlag + 4;
+constexpr uint32_t kTmemCols = 256;
+constexpr int kCtasPerSm = 2;
+
+// Digit i of a value whose 56-bit aligned magnitude is F, as the FP32 number
+// +-d_i 2^(-7 i): d_i is placed in mantissa bits 16..22 of a float of
+// exponent 2^(7 - 7 i) (with the value's sign) and that float's leading 1
+// is subtracted off (exact).
+template <int I>
+__device__ __forceinline__ float digit(unsigned long long F, uint32_t sgn) {
+  constexpr int sh = 33 - 7 * I;  // moves bits 49 - 7 I .. 55 - 7 I to 16 .. 22
+  const uint32_t f = sh >= 0 ? (uint32_t)(F >> (sh >= 0 ? sh : 0)) : (uint32_t)(F << (sh < 0 ? -sh : 0));
+  const uint32_t bias = ((uint32_t)(134 - 7 * I) << 23) | sgn;
+  return __uint_as_float((f & 0x7f0000u) | bias) - __uint_as_float(bias);
+}
+
+// The eight digits of v aligned to biased exponent E (v's exponent <= E):
+// the significand shifted right by E - e_v and rounded to nearest (ties
+// away from zero), so F < 2^56 and the alignment error is unbiased. Zeros
+// and subnormals (exponent field 0) give zero digits.
+__device__ __forceinline__ void digits8(double v, int E, float d[kDigits]) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t sgn = hi & 0x80000000u;
+  const int ev = (int)((hi >> 20) & 0x7ffu);
+  const int sh = E - ev;
+  const unsigned long long M3 = (((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) << 3;
+  const unsigned long long F =
+      (ev == 0 || sh > 56) ? 0ull : sh == 0 ? M3 : (((M3 >> (sh - 1)) + 1ull) >> 1);
+  d[0] = digit<0>(F, sgn);
+  d[1] = digit<1>(F, sgn);
+  d[2] = digit<2>(F, sgn);
+  d[3] = digit<3>(F, sgn);
+  d[4] = digit<4>(F, sgn);
+  d[5] = digit<5>(F, sgn);
+  d[6] = digit<6>(F, sgn);
+  d[7] = digit<7>(F, sgn);
+}
+
+__device__ __forceinline__ uint32_t abs_hi(double v) { return (uint32_t)__double2hiint(v) & 0x7fffffffu; }
+
+// Stores the digit words of 4 consecutive complex entries (one 16-byte chunk
+// of every digit operand's row).
+__device__ __forceinline__ void store_chunk(const double2 x[4], int E, uint32_t row_chunk, uint32_t digit_bytes) {
+  uint32_t w[kDigits][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float dr[kDigits], di[kDigits];
+    digits8(x[e].x, E, dr);
+    digits8(x[e].y, E, di);
+#pragma unroll
+    for (int i = 0; i < kDigits; ++i) w[i][e] = pack_bf16x2(dr[i], di[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < kDigits; ++i) sts128(row_chunk + i * digit_bytes, w[i][0], w[i][1], w[i][2], w[i][3]);
+}
+
+// Entry (i, j) of the 16 x 16 superoperator the pass applies: S itself, or
+// S (x) I for a width-1 block S (4 x 4) embedded on local qubit 0 (local
+// index l = r0 + 2 r1 + 4 c0 + 8 c1; the identity acts on qubit 1).
+__device__ __forceinline__ double2 sop_entry(const double2* S, int embed, int i, int j) {
+  if (!embed) return S[i * 16 + j];
+  if (((i >> 1) & 1) != ((j >> 1) & 1) || ((i >> 3) & 1) != ((j >> 3) & 1)) return make_double2(0.0, 0.0);
+  const int a = (i & 1) | ((i >> 1) & 2), b = (j & 1) | ((j >> 1) & 2);
+  return S[a * 4 + b];
+}
+
+// B operand: the digits of R (32 x 32 real, row n = 2 o + (0: Re, 1: Im) of
+// output o, column k = 2 l + (0: Re, 1: Im) of input l) with per-row
+// alignment. Thread t (128 threads) slices row n = t / 4, inputs l = 4 (t %
+// 4) .. +3 (one 16-byte chunk of every digit row); s_G[n] receives G_n.
+__device__ __forceinline__ void build_b_digits(unsigned char* smem, uint32_t sbase, const double2* S, int embed,
+                                               int tid) {
+  const int n = tid >> 2, quarter = tid & 3, o = n >> 1;
+  double2 r[4];
+  uint32_t mx = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const double2 s = sop_entry(S, embed, o, 4 * quarter + e);
+    r[e] = (n & 1) ? make_double2(s.y, s.x) : make_double2(s.x, -s.y);  // Im y = Si xr + Sr xi; Re y = Sr xr - Si xi
+    mx = max(mx, max(abs_hi(r[e].x), abs_hi(r[e].y)));
+  }
+  mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  const int G = (int)(mx >> 20);
+  if (quarter == 0) reinterpret_cast<int*>(smem + kOffG)[n] = G;
+  store_chunk(r, G, sbase + kOffB + core_off(n, quarter), kBTermBytes);
+}
+
+// 64-bit integer multiply-add of a 32-bit word: c + a * b (unsigned, mod 2^64).
+__device__ __forceinline__ unsigned long long mad_wide(uint32_t a, uint32_t b, unsigned long long c) {
+  unsigned long long d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// FP32 bit pattern of 1.5 * 2^(23 - u): adding it to a multiple of 2^-u below
+// 2^(22 - u) in magnitude leaves that multiple, in units of 2^-u, plus 2^22 in
+// the low mantissa bits (exact).
+__host__ __device__ constexpr uint32_t magic_bits(int u) { return ((uint32_t)(150 - u) << 23) | 0x400000u; }
+
+// sum over the accumulators of the magic patterns at their weights (mod
+// 2^64), subtracted once from the combined raw patterns
+__host__ __device__ constexpr unsigned long long magic_offset() {
+  return ((unsigned long long)magic_bits(0) << 42) + ((unsigned long long)magic_bits(7) << 35) +
+         ((unsigned long long)magic_bits(14) << 28) + ((unsigned long long)magic_bits(21) << 21) +
+         ((unsigned long long)magic_bits(28) << 14) + ((unsigned long long)magic_bits(35) << 7) +
+         (unsigned long long)magic_bits(42);
+}
+
+// Real output from its 7 accumulator values (orders 0..5, then 6 + 7): the
+// exact integer sum in units of 2^-42 of order 0, converted and scaled by
+// 2^(E + G - 2100).
+__device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
+  const uint32_t b0 = __float_as_uint(c[0] + __uint_as_float(magic_bits(0)));
+  const uint32_t b1 = __float_as_uint(c[1] + __uint_as_float(magic_bits(7)));
+  const uint32_t b2 = __float_as_uint(c[2] + __uint_as_float(magic_bits(14)));
+  const uint32_t b3 = __float_as_uint(c[3] + __uint_as_float(magic_bits(21)));
+  const uint32_t b4 = __float_as_uint(c[4] + __uint_as_float(magic_bits(28)));
+  const uint32_t b5 = __float_as_uint(c[5] + __uint_as_float(magic_bits(35)));
+  const uint32_t bq = __float_as_uint(c[6] + __uint_as_float(magic_bits(42)));
+  unsigned long long Z = (unsigned long long)(b0 * 128u + b1) << 35;  // wraps mod 2^64 like the rest
+  Z = mad_wide(b2, 1u << 28, Z);
+  Z = mad_wide(b3, 1u << 21, Z);
+  Z = mad_wide(b4, 1u << 14, Z);
+  Z = mad_wide(b5, 1u << 7, Z);
+  Z += bq;
+  Z -= magic_offset();
+  double dz;
+  asm("cvt.rn.f64.s64 %0, %1;" : "=d"(dz) : "l"((long long)Z));
+  const uint32_t zh = (uint32_t)__double2hiint(dz);
+  const int ez = (int)((zh >> 20) & 0x7ffu);
+  if (ez == 0 || ez + scale <= 0) return 0.0;  // zero, or below the normal range (|y| < 2^-1022)
+  return __hiloint2double((int)(zh + ((uint32_t)scale << 20)), __double2loint(dz));
+}
+
+struct Group {
+  unsigned int rb, cb;
+  bool active, self;
+};
+
+// max_tries: try_wait rounds before an MMA wait gives up; skip_mma (tests
+// of the failure path only): issue neither the MMAs nor their commit.
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2* rho, const double2* __restrict__ S,
+                                                                           const __grid_constant__ ApplyParams p,
+                                                                           int embed, long long max_tries,
+                                                                           int skip_mma) {
+  constexpr int D = 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t bar = sbase + kOffBar;
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kOffFlag);
+  const int* s_G = reinterpret_cast<const int*>(smem + kOffG);
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+
+  int qs[2] = {p.q[0], p.q[1]};
+  if (qs[0] > qs[1]) {
+    const int t = qs[0];
+    qs[0] = qs[1];
+    qs[1] = t;
+  }
+  const unsigned int b0 = 1u << p.q[0], b1 = 1u << p.q[1], N = 1u << p.n;
+  build_b_digits(smem, sbase, S, embed, tid);
+  if (tid == 0) {
+    bar_init(bar, 1);
+    *s_abort = 0;
+  }
+  if (w == 0) tmem_alloc(sbase + kOffTmem, kTmemCols);
+  fence_operands();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+
+  // a warp covers 8 row rests x 4 column rests of the half tile
+  const int i = (lane % 8) + 8 * (w % 2), j0 = (lane / 8) + 4 * (w / 2);
+  const unsigned int di = (unsigned int)deposit_zeros(i, qs, 2), dj0 = (unsigned int)deposit_zeros(j0, qs, 2),
+                     dj1 = (unsigned int)deposit_zeros(j0 + 8, qs, 2);
+  const uint32_t a_row = sbase + kOffA + core_off(tid, 0);
+  const uint32_t t_row = tmem + ((uint32_t)(32 * w) << 16);  // this warp's 32 TMEM lanes
+  const unsigned long long Mt = (1ull << (p.n - 2)) / kTile;
+  const unsigned long long n_units = Mt * (Mt + 1);
+
+  auto group_of = [&](unsigned long long u) {
+    bool diag = false;
+    const unsigned long long tt = canonical_group(u >> 1, 32, &diag);
+    const int j = (int)(u & 1ull) * 8 + j0;
+    Group g;
+    g.active = !(diag && i > j);
+    g.self = diag && i == j;
+    g.rb = (unsigned int)deposit_zeros((tt & 0xffffffffull) * kTile, qs, 2) + di;
+    g.cb = (unsigned int)deposit_zeros((tt >> 32) * kTile, qs, 2) + ((u & 1ull) ? dj1 : dj0);
+    return g;
+  };
+  auto load = [&](const Group& g, double2 x[D]) {
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      bool up;
+      const unsigned int idx = entry_index(g.rb, g.cb, l, b0, b1, N, &up);
+      x[l] = g.active ? rho[idx] : make_double2(0.0, 0.0);
+    }
+  };
+
+  unsigned long long u = blockIdx.x;
+  Group gn{};
+  double2 xn[D];
+  if (u < n_units) {
+    gn = group_of(u);
+    load(gn, xn);
+  }
+  uint32_t phase = 0;
+#pragma unroll 1
+  for (; u < n_units; u += gridDim.x, phase ^= 1u) {
+    const Group g = gn;
+    double2 x[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) x[l] = xn[l];
+    if (u + gridDim.x < n_units) {
+      gn = group_of(u + gridDim.x);
+      load(gn, xn);
+    }
+    // entries read from their transposes are conjugated; the group's
+    // alignment is its largest exponent
+    uint32_t mx = 0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      bool up;
+      (void)entry_index(g.rb, g.cb, l, b0, b1, N, &up);
+      if (!up) x[l].y = -x[l].y;
+      mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
+    }
+    const int E = (int)(mx >> 20);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) store_chunk(x + 4 * c, E, a_row + c * 128u, kADigitBytes);
+    fence_operands();
+    fence_before_sync();
+    __syncthreads();
+    if (*s_abort) break;
+    if (tid == 0 && !skip_mma) {
+      fence_after_sync();
+      // accumulator a <- the digit pairs of order t = a (a < 6); accumulator
+      // 6 <- order 7, then order 6 (smallest first). The first MMA of each
+      // accumulator overwrites it.
+      const int order_of[8] = {0, 1, 2, 3, 4, 5, 7, 6};
+#pragma unroll 1
+      for (int s = 0; s < 8; ++s) {
+        const int t = order_of[s];
+        const uint32_t d_acc = tmem + (uint32_t)(32 * (t < 6 ? t : 6));
+#pragma unroll 1
+        for (int ia = 0; ia <= t; ++ia) {  // digit ia of x times digit t - ia of R (t <= 7 < kDigits)
+#pragma unroll
+          for (int kh = 0; kh < 2; ++kh)
+            mma_bf16(d_acc, smem_desc(sbase + kOffA + ia * kADigitBytes + kh * 256),
+                     smem_desc(sbase + kOffB + (t - ia) * kBTermBytes + kh * 256),
+                     (s != 7 && ia == 0 && kh == 0) ? 0u : 1u);
+        }
+      }
+      commit(bar);
+    }
+    const bool waited = bar_wait(bar, phase, max_tries);
+    if (!waited) {
+      atomicAdd(&g_oz_timeouts, 1u);
+      *s_abort = 1;  // every thread leaves at the next unit's barrier
+    }
+    // warp-collective accumulator reads only when every lane saw the MMAs
+    // complete; otherwise rho keeps this unit's old entries and the timeout
+    // is reported by the next readout
+    if (!__all_sync(0xffffffffu, waited)) continue;
+    fence_after_sync();
+#pragma unroll 1
+    for (int ch = 0; ch < 4; ++ch) {  // 8 real outputs (4 entries) per chunk
+      float cv[kAccs][8];
+#pragma unroll
+      for (int a = 0; a < kAccs; ++a) tmem_ld8(t_row + (uint32_t)(32 * a + 8 * ch), cv[a]);
+      if (!g.active) continue;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int o = 4 * ch + e;
+        float cr[kAccs], ci[kAccs];
+#pragma unroll
+        for (int a = 0; a < kAccs; ++a) {
+          cr[a] = cv[a][2 * e];
+          ci[a] = cv[a][2 * e + 1];
+        }
+        double2 y;
+        y.x = recombine(cr, E + s_G[2 * o] - 2100);
+        y.y = recombine(ci, E + s_G[2 * o + 1] - 2100);
+        bool up;
+        const unsigned int idx = entry_index(g.rb, g.cb, o, b0, b1, N, &up);
+        if (up) {
+          rho[idx] = y;
+        } else if (!g.self) {  // a self-conjugate group writes its upper entries only
+          y.y = -y.y;
+          rho[idx] = y;
+        }
+      }
+    }
+    fence_before_sync();
+  }
+  __syncthreads();
+  // after a timeout the unit's MMAs may still be in flight: wait for them
+  // (bounded) before the tensor memory is released
+  if (*s_abort && tid == 0) bar_wait(bar, phase ^ 1u, max_tries);
+  __syncthreads();
+  if (w == 0) {
+    fence_after_sync();
+    tmem_free(tmem, kTmemCols);
+  }
+}
+
+}  // namespace
+
+bool oz_eligible(int n, int width) { return (width == 1 || width == 2) && n - 2 >= 4; }
+
+cudaError_t launch_herm_oz(double2* rho, const double2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
+  if (!oz_eligible(p.n, p.width)) return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(k_apply_herm_oz2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  if (attr != cudaSuccess) return attr;
+  ApplyParams q = p;
+  int embed = 0;
+  if (p.width == 1) {
+    // S (x) I on (q, q'): the second qubit is the highest other qubit
+    embed = 1;
+    q.width = 2;
+    q.q[1] = p.q[0] == p.n - 1 ? p.n - 2 : p.n - 1;
+  }
+  long long tries = 0;
+  int skip = 0;
+  tc_test_limits(&tries, &skip);
+  const unsigned long long Mt = (1ull << (p.n - 2)) / kTile, n_units = Mt * (Mt + 1);
+  const int grid = (int)std::max<unsigned long long>(
+      1, std::min<unsigned long long>(n_units, (unsigned long long)num_sms * kCtasPerSm));
+  k_apply_herm_oz2<<<grid, kThreads, kSmemBytes, st>>>(rho, S, q, embed, tries, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_take_timeouts(unsigned int* count, cudaStream_t st) {
+  unsigned int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(count, g_oz_timeouts, sizeof(unsigned int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && *count) {
+    e = cudaMemcpyToSymbolAsync(g_oz_timeouts, &zero, sizeof(unsigned int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return e;
+}
+
+}  // namespace tq

@@ -217,6 +217,11 @@ cudaError_t launch_herm_tc2(float2* rho, const float2* S, const ApplyParams& p, 
   return cudaGetLastError();
 }
 
+void tc_test_limits(long long* max_tries, int* skip_mma) {
+  *max_tries = g_test_max_tries.load();
+  *skip_mma = g_test_skip_mma.load();
+}
+
 cudaError_t tc_take_timeouts(unsigned int* count, cudaStream_t st) {
   unsigned int zero = 0;
   cudaError_t e = cudaMemcpyFromSymbolAsync(count, g_tc_timeouts, sizeof(unsigned int), 0, cudaMemcpyDeviceToHost, st);

@@ -164,5 +164,13 @@ cudaError_t launch_herm_tc2(float2* rho, const float2* S, const ApplyParams& p, 
 // Bounded tensor-core waits that gave up since the last call (any state on
 // the current device); clears the count. Synchronises `st`.
 cudaError_t tc_take_timeouts(unsigned int* count, cudaStream_t st);
+// Failure-path test settings of the tensor-core passes (tq_test_tc_wait_limit).
+void tc_test_limits(long long* max_tries, int* skip_mma);
+// FP64 states, widths 1-2, Hermitian mode: the FP64-accurate pass on the
+// tcgen05 tensor cores (tq_apply_oz.cu; a width-1 block runs as S (x) I);
+// needs n - 2 >= 4. S: the block's FP64 superoperator (4^w x 4^w).
+bool oz_eligible(int n, int width);
+cudaError_t launch_herm_oz(double2* rho, const double2* S, const ApplyParams& p, int num_sms, cudaStream_t st);
+cudaError_t oz_take_timeouts(unsigned int* count, cudaStream_t st);
 
 }  // namespace tq

@@ -21,12 +21,17 @@ namespace {
 // Kernel kinds for launch counting and event profiling.
 enum Kind {
   K_BUILD = 0, K_FUSE, K_REDUCE, K_APPLY64 /* +w-1 */, K_APPLY32 = K_APPLY64 + 4, K_PACK = K_APPLY32 + 4,
-  K_SPARSE64 /* +w-1 */, K_NKINDS = K_SPARSE64 + 2
+  K_SPARSE64 /* +w-1 */, K_TC64 = K_SPARSE64 + 2 /* +w-1 */, K_NKINDS = K_TC64 + 2
 };
 const char* kKindName[K_NKINDS] = {"superop_build", "fuse",         "reduce",        "apply_f64_w1",
                                    "apply_f64_w2",  "apply_f64_w3", "apply_f64_w4",  "apply_f32_w1",
                                    "apply_f32_w2",  "apply_f32_w3", "apply_f32_w4",  "sparse_pack",
-                                   "apply_f64_sparse_w1", "apply_f64_sparse_w2"};
+                                   "apply_f64_sparse_w1", "apply_f64_sparse_w2", "apply_f64tc_w1",
+                                   "apply_f64tc_w2"};
+
+// Whether FP64 passes of widths <= 2 run on the tensor cores when the
+// engine is TQ_ENGINE_AUTO.
+constexpr bool kAutoTensor = false;
 
 struct Pending {
   int kind;
@@ -92,6 +97,7 @@ struct tq_state {
   bool herm_ok = true;       // rho is known to be Hermitian
   bool lower_stale = false;  // entries with row > column are out of date
   bool tc_used = false;      // a tensor-core pass (bounded waits) was enqueued
+  int fp64_engine = TQ_ENGINE_AUTO;  // products of FP64 passes (tq_set_fp64_engine)
   uint64_t launches = 0;
   bool prof_on = false;
   std::vector<Pending> pending;
@@ -162,6 +168,10 @@ void free_buf(DevBuf& b) {
 
 size_t entry_bytes(int prec) { return prec == TQ_FP64 ? 16 : 8; }
 
+bool fp64_on_tensor(const tq_state* s) {
+  return s->fp64_engine == TQ_ENGINE_TENSOR || (s->fp64_engine == TQ_ENGINE_AUTO && kAutoTensor);
+}
+
 tq_status check_state(tq_state* s) {
   if (!s) return TQ_ERR_ARG;
   if (s->poisoned) return TQ_ERR_STATE;
@@ -173,10 +183,11 @@ tq_status check_state(tq_state* s) {
 tq_status readout_done(tq_state* s, cudaError_t e) {
   if (e != cudaSuccess) return cuda_fail(s, e);
   if (!s->tc_used) return TQ_OK;
-  unsigned int timeouts = 0;
+  unsigned int timeouts = 0, oz = 0;
   e = tc_take_timeouts(&timeouts, s->stream);
+  if (e == cudaSuccess) e = oz_take_timeouts(&oz, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e);
-  if (timeouts) {
+  if (timeouts || oz) {
     s->poisoned = true;
     return TQ_ERR_TIMEOUT;
   }
@@ -456,12 +467,20 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
       if (e != cudaSuccess) break;
     }
     const void* S = s->prec == TQ_FP64 ? (const void*)(sb64 + P.sb_off[b]) : (const void*)(sb32 + P.sb_off[b]);
-    const bool sparse = p.sparse && s->prec == TQ_FP64 && P.sp_slot[b] >= 0;
+    // FP64 blocks of widths <= 2 on the tensor cores (FP64-accurate slicing)
+    const bool oz = herm && s->prec == TQ_FP64 && fp64_on_tensor(s) && oz_eligible(s->n, p.width);
+    const bool sparse = !oz && p.sparse && s->prec == TQ_FP64 && P.sp_slot[b] >= 0;
     if (!sparse) p.sparse = 0;
-    const int kind = sparse ? K_SPARSE64 + p.width - 1 : (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
+    const int kind = oz ? K_TC64 + p.width - 1
+                        : sparse ? K_SPARSE64 + p.width - 1 : (s->prec == TQ_FP64 ? K_APPLY64 : K_APPLY32) + p.width - 1;
     const SparseBlock* spb = sparse ? sps + P.sp_slot[b] : nullptr;
-    if (herm && s->prec == TQ_SPLIT && p.width == 2) s->tc_used = true;
-    e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream, spb); });
+    if (herm && ((s->prec == TQ_SPLIT && p.width == 2) || oz)) s->tc_used = true;
+    if (oz)
+      e = timed(s, kind, 1, [&] {
+        return launch_herm_oz(static_cast<double2*>(s->rho), static_cast<const double2*>(S), p, s->num_sms, s->stream);
+      });
+    else
+      e = timed(s, kind, 1, [&] { return launch_apply(s->rho, s->prec, S, p, s->num_sms, s->stream, spb); });
     if (s->prof_on) {  // per launch: the groups computed x (8 * 16^w flops, 2 * B * 4^w bytes) each
       const int per = 1 << (2 * p.width);
       if (sparse)  // 8 flops per nonzero of the row lists the kernel applied
@@ -683,6 +702,18 @@ tq_status tq_rho_device_ptr(tq_state* s, void** out) {
   return TQ_OK;
 }
 
+tq_status tq_set_fp64_engine(tq_state* s, int engine) {
+  if (!s || engine < TQ_ENGINE_AUTO || engine > TQ_ENGINE_TENSOR) return TQ_ERR_ARG;
+  s->fp64_engine = engine;
+  return TQ_OK;
+}
+
+tq_status tq_fp64_on_tensor(const tq_state* s, int* on_tensor) {
+  if (!s || !on_tensor) return TQ_ERR_ARG;
+  *on_tensor = fp64_on_tensor(s) ? 1 : 0;
+  return TQ_OK;
+}
+
 tq_status tq_set_hermitian(tq_state* s, int on) {
   tq_status st = check_state(s);
   if (st != TQ_OK) return st;
@@ -833,7 +864,7 @@ tq_status tq_program_run(tq_state* s, const tq_program* p) {
     if (e != cudaSuccess) return cuda_fail(s, e);
     p->g_blk_ready = true;
   }
-  const int key = (s->herm_mode && s->herm_ok ? 1 : 0) | (s->lower_stale ? 2 : 0);
+  const int key = (s->herm_mode && s->herm_ok ? 1 : 0) | (s->lower_stale ? 2 : 0) | (fp64_on_tensor(s) ? 4 : 0);
   if (!(p->g_exec && p->g_rho == s->rho && p->g_key == key)) {
     // (re)capture the launch sequence on a private stream; the state's flags
     // and launch count advance as if it ran, which is what the graph does

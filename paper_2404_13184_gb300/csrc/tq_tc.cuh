@@ -1,5 +1,6 @@
-// tcgen05 building blocks of the split-precision width-2 pass on the tensor
-// cores (sm_103a), used by the single-state kernel (tq_apply_tc.cu).
+// tcgen05 building blocks of the tensor-core apply passes (sm_103a): the
+// split-precision width-2 pass (tq_apply_tc.cu) and the FP64-accurate pass
+// (tq_apply_oz.cu).
 //
 // The product y = S x of a width-2 block is a dense 16 x 16 complex
 // matrix-vector product per group (TANQ-Sim Sec. 3.1, the C2 update; its
@@ -155,6 +156,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
 // B operand of a width-2 block: (R - I) in three BF16 terms at `b` (shared

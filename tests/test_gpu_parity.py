@@ -207,7 +207,7 @@ def test_ghz_depolarizing_closed_form_at_12q(tq):
     assert abs(zz[2]) < TOL64
 
 
-def _factorised_check(tq, n, subset, width, precision, n_gates, seed, n_samples=4096, tol=TOL64):
+def _factorised_check(tq, n, subset, width, precision, n_gates, seed, n_samples=4096, tol=TOL64, engine=None):
     """Full-size check: a product state (random SU(2) + amplitude damping on
     every qubit), then a noisy circuit on `subset` only. rho factorises into
     the oracle's small results, so sampled entries of the 4^n vector can be
@@ -227,7 +227,7 @@ def _factorised_check(tq, n, subset, width, precision, n_gates, seed, n_samples=
     ops_s = [(nm, [local[qs[0]]], pr) for nm, qs, pr in prefix if qs[0] in local] + sub.ops
     rho_s = O.run_circuit(len(subset), ops_s)
 
-    with tq.State(n, precision) as st:
+    with tq.State(n, precision, engine=engine) as st:
         st.run(prefix + body, width=width)
         tr = st.trace()
         st.device_ptr()                                  # every entry current (Hermitian mode)
