@@ -235,10 +235,11 @@ def step_ops():
     return workloads.tfim_ring(N_QUBITS, steps=1).ops
 
 
-def run_device_leg(tq, torch, precision, steps, warmup, world, clocks=None):
+def run_device_leg(tq, torch, precision, steps, warmup, world, clocks=None, engine="auto"):
     """K timed steps from device-resident inputs; returns timings and stats."""
     import torch.distributed as dist
-    st = tq.State(N_QUBITS, precision)
+    st = tq.State(N_QUBITS, precision, engine=engine)
+    on_tensor = st.fp64_on_tensor() if precision == "fp64" else False
     prog = tq.DeviceProgram(N_QUBITS, step_ops(), width=-1, precision=precision)
     masks = torch.tensor([ZZ_MASK], dtype=torch.int64, device="cuda")
     out = torch.zeros(warmup + steps, dtype=torch.float64, device="cuda")
@@ -271,16 +272,18 @@ def run_device_leg(tq, torch, precision, steps, warmup, world, clocks=None):
     st.profile(False)
     zz = out.cpu().tolist()
     res = {"ms": ms, "launches": launches, "stats": stats, "zz": zz, "blocks": prog.n_blocks,
-           "max_width": prog.max_width, "table_bytes": prog.table_bytes, "clocks": clk}
+           "max_width": prog.max_width, "table_bytes": prog.table_bytes, "clocks": clk, "on_tensor": on_tensor}
     prog.free()
     st.free()
     return res
 
 
-def run_e2e_leg(tq, torch, precision, steps, warmup, world):
-    """The public host-buffer API: tq_run_circuit + tq_expect_z per step."""
+def run_e2e_leg(tq, torch, precision, steps, warmup, world, engine="auto", profile=False):
+    """The public host-buffer API: tq_run_circuit + tq_expect_z per step.
+    Returns ms for the K steps (and, with profile, the per-kernel stats and
+    the <Z0 Z1> of every step)."""
     import torch.distributed as dist
-    st = tq.State(N_QUBITS, precision)
+    st = tq.State(N_QUBITS, precision, engine=engine)
     prog = tq.Program(step_ops())
     for _ in range(warmup):
         st.run(prog, width=-1)
@@ -288,16 +291,48 @@ def run_e2e_leg(tq, torch, precision, steps, warmup, world):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    if profile:
+        st.profile(True)
+    zz = []
     t0 = time.perf_counter()
     for _ in range(steps):
         st.run(prog, width=-1)
-        st.expect_z([ZZ_MASK])
+        zz.append(float(st.expect_z([ZZ_MASK])[0]))
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     if world > 1:
         dist.barrier()
+    stats = st.profile_stats() if profile else None
     st.free()
+    if profile:
+        return dt * 1e3, stats, zz
     return dt * 1e3
+
+
+def fp64_roofline(name, st, pipes, sm_max, sm_mhz, sms, hbm_gbs, peak_src):
+    """Roofline of the dominant FP64 apply kernel: the tensor-core engine's
+    passes are bound by HBM (algorithmic bytes: one read and one write of
+    every canonical entry), the DFMA kernels by the FP64 pipe (algorithmic
+    flops: 8 per applied complex multiply-add)."""
+    avg_ms = st["total_ms"] / st["launches"]
+    if "f64tc" in name:
+        ach = st["bytes"] / (avg_ms / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": ach / hbm_gbs, "traffic": traffic_from_profile(name),
+                "algorithmic_bytes_per_launch": st["bytes"], "algorithmic_flops_per_launch": st["flops"],
+                "launches": st["launches"], "avg_launch_ms": avg_ms, "peak_source": f"{peak_src} HBM copy bandwidth",
+                "fp64_pipe_frac_equivalent": st["flops"] / (avg_ms / 1e3) / 1e12 / pipes["dfma"]}
+    ach = st["flops"] / (avg_ms / 1e3) / 1e12
+    peak = fp64_peak_tflops(sm_max, sms)
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic_from_profile(name),
+            "algorithmic_bytes_per_launch": st["bytes"], "algorithmic_flops_per_launch": st["flops"],
+            "flops_count": "8 per nonzero of the row lists the kernel applied (read back from the device), per "
+                           "canonical group" if "sparse" in name else "dense 8 x 16^w per canonical group",
+            "launches": st["launches"], "avg_launch_ms": avg_ms,
+            "peak_source": f"DFMA pipe, nominal: {sms} SMs x 4 FP64 flop/clk x {sm_max:.0f} MHz",
+            "frac_at_measured_clock": ach / fp64_peak_tflops(sm_mhz, sms),
+            "peak_measured_dfma": pipes["dfma"], "frac_of_measured_dfma": ach / pipes["dfma"]}
 
 
 def dominant(stats: dict):
@@ -875,6 +910,10 @@ def main():
                     help="arrival window (s) of the served streams added to the tfim15 line (0: none)")
     ap.add_argument("--serve-drain-in-line", type=float, default=20.0,
                     help="drain window (s) after the in-line served streams' arrivals stop")
+    ap.add_argument("--fp64-engine", default="auto", choices=["auto", "dfma", "tensor"],
+                    help="products of the FP64 apply passes (tq_set_fp64_engine)")
+    ap.add_argument("--no-dfma-leg", action="store_true",
+                    help="leave out the DFMA-engine comparison when the FP64 leg runs on the tensor cores")
     ap.add_argument("--no-extras", action="store_true",
                     help="tfim15 line only: leave out the plain6, layered12, sweep and serve objects")
     args = ap.parse_args()
@@ -951,28 +990,32 @@ def main():
     K, W = args.steps, args.warmup
     K64 = args.fp64_steps or K
     gates_per_step = 2 * N_QUBITS
-    fp64 = run_device_leg(tq, torch, "fp64", K64, W, world, Clocks(gpu_index))
+    fp64 = run_device_leg(tq, torch, "fp64", K64, W, world, Clocks(gpu_index), engine=args.fp64_engine)
     split = None if args.no_split else run_device_leg(tq, torch, "split", K, W, world)
-    e2e_ms = None if args.no_e2e else run_e2e_leg(tq, torch, "fp64", K64, W, world)
+    e2e_ms = None if args.no_e2e else run_e2e_leg(tq, torch, "fp64", K64, W, world, engine=args.fp64_engine)
 
     ms64 = max_over_ranks(fp64["ms"], world)
     value = job_throughput(K64 * gates_per_step, ms64, world)
     clk = fp64["clocks"] or {}
     sm_mhz = clk.get("sm_mhz") or sm_max_cfg
-    name64, st64 = dominant(fp64["stats"])
     sms = device_sms()
-    ach64 = st64["flops"] * st64["launches"] / (st64["total_ms"] / 1e3) / 1e12
     pipes = {p_: measured_pipe(tq, p_) for p_ in ("dfma", "dmma", "ffma", "cvt_f64_s64", "cvt_f64_f32")}
-    peak64 = fp64_peak_tflops(sm_max_cfg, sms)
-    roof = {"kernel": name64, "bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
-            "frac": ach64 / peak64, "traffic": traffic_from_profile(name64),
-            "algorithmic_bytes_per_launch": st64["bytes"], "algorithmic_flops_per_launch": st64["flops"],
-            "flops_count": "8 per nonzero of the row lists the kernel applied (read back from the device), per "
-                           "canonical group" if "sparse" in name64 else "dense 8 x 16^w per canonical group",
-            "launches": st64["launches"], "avg_launch_ms": st64["total_ms"] / st64["launches"],
-            "peak_source": f"DFMA pipe, nominal: {sms} SMs x 4 FP64 flop/clk x {sm_max_cfg:.0f} MHz",
-            "frac_at_measured_clock": ach64 / fp64_peak_tflops(sm_mhz, sms),
-            "peak_measured_dfma": pipes["dfma"], "frac_of_measured_dfma": ach64 / pipes["dfma"]}
+    name64, st64 = dominant(fp64["stats"])
+    roof = fp64_roofline(name64, st64, pipes, sm_max_cfg, sm_mhz, sms, hbm_gbs, peak_src)
+    dfma_leg = None
+    if fp64["on_tensor"] and not args.no_dfma_leg:
+        # the same step on the DFMA engine (tq_run_circuit, planned for it):
+        # its apply passes beside the tensor-core ones
+        k_d = max(3, K64 // 4)
+        ms_d, st_d, zz_d = run_e2e_leg(tq, torch, "fp64", k_d, W, world, engine="dfma", profile=True)
+        nd, sd = dominant(st_d)
+        n_cmp = min(len(zz_d), len(fp64["zz"]))
+        dfma_leg = {"value": job_throughput(k_d * gates_per_step, max_over_ranks(ms_d, world), world), "unit": UNIT,
+                    "ms_per_step": ms_d / k_d, "steps": k_d, "api": "tq_run_circuit (host tables)",
+                    "zz_max_abs_diff_vs_tensor_engine": max(abs(a - b) for a, b in zip(zz_d[:n_cmp], fp64["zz"][:n_cmp])),
+                    "roofline": fp64_roofline(nd, sd, pipes, sm_max_cfg, sm_mhz, sms, hbm_gbs, peak_src),
+                    "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["total_ms"] / v["launches"], 4)}
+                                for k, v in st_d.items() if k.startswith("apply")}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K64, "warmup": W,
             "ms_per_step": ms64 / K64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -986,6 +1029,7 @@ def main():
                        "l2": "inputs larger than L2 (16 GiB rho), no flush", "parallelism": "replicas"
                        if world > 1 else "single"},
             "roofline": roof, "gpu_launches": fp64["launches"],
+            "fp64_engine": "tensor (tcgen05, fixed-point digit slicing)" if fp64["on_tensor"] else "dfma",
             "pipes_measured": {"dfma_tflops": pipes["dfma"], "dmma_tflops": pipes["dmma"], "ffma_tflops": pipes["ffma"],
                                "cvt_f64_s64_tops": pipes["cvt_f64_s64"], "cvt_f64_f32_tops": pipes["cvt_f64_f32"],
                                "how": "tq_pipe_rate: 8 independent chains per thread, 4 x 256 threads per SM on "
@@ -994,6 +1038,8 @@ def main():
                        "reasons": clk.get("reasons", []), "samples": clk.get("samples")},
             "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)}
                         for k, v in fp64["stats"].items()}}
+    if dfma_leg is not None:
+        line["fp64_dfma"] = dfma_leg
     if e2e_ms is not None:
         e2e_ms = max_over_ranks(e2e_ms, world)
         line["e2e"] = {"value": job_throughput(K64 * gates_per_step, e2e_ms, world), "unit": UNIT,

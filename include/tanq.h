@@ -268,7 +268,9 @@ tq_status tq_probs(tq_state* s, double* out);
 typedef struct tq_program tq_program; /* opaque; owns device copies of its tables */
 
 /* Validate ops for an n-qubit register of the given precision, plan the
- * fusion (max_fuse_width as in tq_run_circuit) and upload the Kraus sets and
+ * fusion (max_fuse_width as in tq_run_circuit; the automatic width follows
+ * the cost model of the default FP64 engine, TQ_ENGINE_AUTO, whereas
+ * tq_run_circuit follows the state's engine) and upload the Kraus sets and
  * plan tables to device memory once (synchronously). Running the program
  * then re-does the superoperator build, the fusion and the apply passes from
  * device-resident inputs with no host copies. */

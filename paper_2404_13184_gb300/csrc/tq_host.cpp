@@ -180,7 +180,7 @@ bool op_pattern(const tq_op& op, const ResolvedOp& r, Pattern* out) {
 }
 
 bool block_is_sparse(const Block& b, int precision) {
-  if (precision != TQ_FP64 || !b.has_pat || b.width > 2) return false;
+  if ((precision != TQ_FP64 && precision != kPlanF64Tensor) || !b.has_pat || b.width > 2) return false;
   const int D = 1 << (2 * b.width);
   return pattern_nnz(b.pat) <= kSparseFraction * D * D;
 }
@@ -191,6 +191,10 @@ double block_cost(int width, int precision, int nnz) {
   // A width-k pass moves 2*B bytes per entry and does 8*4^k flops per entry
   // (dense), or 8 * nnz / 4^k with a sparse FP64 superoperator.
   const double hbm = 6.8e12, dfma = 1.2e12, ffma = 74e12;
+  if (precision == kPlanF64Tensor) {
+    if (width <= 2) return kTensorF64PassFactor * 32.0 / hbm * 1e12;  // any width <= 2: one HBM-bound pass
+    precision = TQ_FP64;                                               // wider blocks: the DFMA kernels
+  }
   const double bytes = precision == TQ_FP64 ? 32.0 : 16.0;
   const int D = 1 << (2 * width);
   const bool sparse = precision == TQ_FP64 && width <= 2 && nnz >= 0 && nnz <= kSparseFraction * D * D;

@@ -65,9 +65,17 @@ tq_status validate_op(int n, const tq_op& op);
 // Resolve a (validated) op into its Kraus set, in FP64.
 tq_status resolve_op(const tq_op& op, ResolvedOp* out);
 
+// Planning-only precision code: FP64 states whose blocks of width <= 2 run
+// on the tensor cores (TQ_ENGINE_TENSOR); their passes are bound by HBM, not
+// by the FP64 pipe, so merging ops into blocks of up to 2 qubits is free.
+constexpr int kPlanF64Tensor = 16;
+// Relative pass time of the tensor-core FP64 engine against an HBM-bound
+// pass at the copy bandwidth (measured on GB300).
+constexpr double kTensorF64PassFactor = 1.5;
+
 // Per-precision cost (arbitrary units per 4^n entries) of one apply pass of
 // a block of the given width; nnz < 0 means dense. Used by the automatic
-// fusion planner.
+// fusion planner; precision is TQ_FP64, TQ_SPLIT or kPlanF64Tensor.
 double block_cost(int width, int precision, int nnz = -1);
 
 // Greedy fusion planner (Sec. 3.3, generalised to blocks of <= max_width

@@ -74,8 +74,10 @@ namespace tq {
 
 ApplyParams apply_params(int n, const Block& B);
 
-// Validate, resolve and plan `ops` into P's host fields and `t`.
-tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t);
+// Validate, resolve and plan `ops` into P's host fields and `t`. f64_tensor:
+// plan FP64 blocks for the tensor-core engine (its cost model).
+tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t,
+                       bool f64_tensor = false);
 
 void pack_blob(const tq_program& P, const HostTables& t, char* h);
 

@@ -291,7 +291,8 @@ struct OpKeyHash {
   }
 };
 
-tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t) {
+tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int width, tq_program* P, HostTables* t,
+                       bool f64_tensor) {
   if (width < -1 || width > kMaxWidth) return TQ_ERR_ARG;
   std::vector<PlanOp> qs(n_ops);
   std::vector<int> uop(n_ops);  // op -> its descriptor (identical named ops share one)
@@ -333,7 +334,8 @@ tq_status plan_program(int n, int prec, const tq_op* ops, size_t n_ops, int widt
     qs[i].pat = upat[uop[i]];
   }
   std::vector<Block> plan;
-  tq_status st = plan_fusion(n, qs, width, prec, &plan);
+  const int plan_prec = prec == TQ_FP64 && f64_tensor && oz_eligible(n, 2) ? kPlanF64Tensor : prec;
+  tq_status st = plan_fusion(n, qs, width, plan_prec, &plan);
   if (st != TQ_OK) return st;
   P->n = n;
   P->prec = prec;
@@ -548,7 +550,7 @@ tq_status run_impl(tq_state* s, const tq_op* ops, size_t n_ops, int width, size_
   if (n_ops == 0) return TQ_OK;
   tq_program plan;
   HostTables t;
-  st = plan_program(s->n, s->prec, ops, n_ops, width, &plan, &t);
+  st = plan_program(s->n, s->prec, ops, n_ops, width, &plan, &t, fp64_on_tensor(s));
   if (st != TQ_OK) return st;
   // reuse the state's scratch buffers for this plan
   tq_program& P = s->scratch;
@@ -824,7 +826,7 @@ tq_status tq_program_create(int n, int precision, const tq_op* ops, size_t n_ops
   tq_program* P = new (std::nothrow) tq_program();
   if (!P) return TQ_ERR_OOM;
   HostTables t;
-  tq_status st = plan_program(n, precision, ops, n_ops, max_fuse_width, P, &t);
+  tq_status st = plan_program(n, precision, ops, n_ops, max_fuse_width, P, &t, kAutoTensor);
   if (st != TQ_OK) {
     delete P;
     return st;
