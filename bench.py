@@ -537,8 +537,8 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
               keep_small=0):
     """Poisson arrivals (`rate` per second for `duration` s) of random noisy
     circuits (n ~ U{5..15}, depth ~ U{50..2000}, 30% CX, depolarising and
-    amplitude damping per request) served by the continuous-batching loop.
-    The FIFO queue is kept in arrival order; a request is materialised and
+    amplitude damping per request) served by the continuous-batching loop,
+    fused by the library's cost model (widths <= 2). The FIFO queue is kept in arrival order; a request is materialised and
     handed to the server when it reaches the head (a lookahead of 8; at most
     one per tick), and its latency is measured from its arrival time to the
     tick that collects its result. Ticks are pipelined (tq_server_step_async):
@@ -566,7 +566,7 @@ def run_serve(tq, precision, rate, duration, drain, seed=SEED_SERVE, rho_budget=
         # tick running on the GPU
         if nxt < len(arrivals) and arrivals[nxt] <= now and queued_in_server < 8:
             c = workloads.served_request(rng)
-            rid = srv.submit(c.n, c.ops, width=2, masks=[1])
+            rid = srv.submit(c.n, c.ops, width=-1, masks=[1])
             inflight[rid] = (arrivals[nxt], c.n, c.n_gates, c.ops if c.n <= 6 else None)
             nxt += 1
             queued_in_server += 1
@@ -990,6 +990,12 @@ def main():
     K, W = args.steps, args.warmup
     K64 = args.fp64_steps or K
     gates_per_step = 2 * N_QUBITS
+    # pipe rates first, on a GPU that has not been loaded yet, with the clocks
+    # sampled while the probes run
+    clk_p = Clocks(gpu_index)
+    clk_p.start()
+    pipes = {p_: measured_pipe(tq, p_) for p_ in ("dfma", "dmma", "ffma", "cvt_f64_s64", "cvt_f64_f32")}
+    pipes_clk = clk_p.stop()
     fp64 = run_device_leg(tq, torch, "fp64", K64, W, world, Clocks(gpu_index), engine=args.fp64_engine)
     split = None if args.no_split else run_device_leg(tq, torch, "split", K, W, world)
     e2e_ms = None if args.no_e2e else run_e2e_leg(tq, torch, "fp64", K64, W, world, engine=args.fp64_engine)
@@ -999,7 +1005,6 @@ def main():
     clk = fp64["clocks"] or {}
     sm_mhz = clk.get("sm_mhz") or sm_max_cfg
     sms = device_sms()
-    pipes = {p_: measured_pipe(tq, p_) for p_ in ("dfma", "dmma", "ffma", "cvt_f64_s64", "cvt_f64_f32")}
     name64, st64 = dominant(fp64["stats"])
     roof = fp64_roofline(name64, st64, pipes, sm_max_cfg, sm_mhz, sms, hbm_gbs, peak_src)
     dfma_leg = None
@@ -1033,7 +1038,7 @@ def main():
             "pipes_measured": {"dfma_tflops": pipes["dfma"], "dmma_tflops": pipes["dmma"], "ffma_tflops": pipes["ffma"],
                                "cvt_f64_s64_tops": pipes["cvt_f64_s64"], "cvt_f64_f32_tops": pipes["cvt_f64_f32"],
                                "how": "tq_pipe_rate: 8 independent chains per thread, 4 x 256 threads per SM on "
-                                      "every SM, best of 3 launches (CUDA events)"},
+                                      "every SM, best of 3 launches (CUDA events)", "clocks": pipes_clk},
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons", []), "samples": clk.get("samples")},
             "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3)}

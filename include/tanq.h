@@ -422,6 +422,14 @@ tq_status tq_server_step(tq_server* s, int* n_live, int* n_queued, int* n_finish
  * tq_server_step is allowed: tq_server_step collects a pending tick first. */
 tq_status tq_server_step_async(tq_server* s, int* n_live, int* n_queued, int* n_finished);
 
+/* Products of FP64 requests (as tq_set_fp64_engine): with the tensor
+ * cores, requests of at least 12 qubits advance through the single-state
+ * tensor-core pass, one launch per fused block after the tick's batch
+ * kernel (split requests of at least 12 qubits always do, their width-2
+ * blocks on the split tensor-core pass); smaller requests stay in the
+ * persistent batch kernel. Applies to ticks launched afterwards. */
+tq_status tq_server_set_fp64_engine(tq_server* s, int engine);
+
 /* GPU time of all collected ticks (CUDA events around each tick's
  * admission, apply and readout work), in milliseconds. */
 tq_status tq_server_gpu_ms(const tq_server* s, double* ms);

@@ -97,6 +97,7 @@ _SIGNATURES = [
     ("tq_server_step", c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     ("tq_server_step_async", c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     ("tq_server_gpu_ms", c_int, [c_void_p, POINTER(c_double)]),
+    ("tq_server_set_fp64_engine", c_int, [c_void_p, c_int]),
     ("tq_server_poll", c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
     ("tq_server_info", c_int, [c_void_p, POINTER(c_size_t), POINTER(ctypes.c_ulonglong),
                                POINTER(ctypes.c_ulonglong)]),
@@ -289,7 +290,7 @@ class Server:
     """Continuous-batching serving loop (tq_server)."""
 
     def __init__(self, precision: str = "fp64", rho_budget: int = 1 << 30, table_budget: int = 1 << 28,
-                 max_live: int = 64, stream=None):
+                 max_live: int = 64, stream=None, engine: str | None = None):
         lib = load()
         self.precision = precision
         torch = _torch_plumbing()
@@ -299,6 +300,8 @@ class Server:
         self._nmasks = {}
         _check(lib.tq_server_create(PRECISION[precision], c_void_p(stream), rho_budget, table_budget, max_live,
                                     ctypes.byref(self._h)), "tq_server_create")
+        if engine is not None:
+            self.set_fp64_engine(engine)
 
     def submit(self, n: int, ops, width: int = -1, masks=()) -> int:
         prog = ops if isinstance(ops, Program) else Program(ops)
@@ -313,6 +316,10 @@ class Server:
         a, b, c = c_int(0), c_int(0), c_int(0)
         _check(_lib.tq_server_step(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "tq_server_step")
         return a.value, b.value, c.value
+
+    def set_fp64_engine(self, engine: str):
+        """'auto', 'dfma' or 'tensor' (tq_server_set_fp64_engine)."""
+        _check(_lib.tq_server_set_fp64_engine(self._h, ENGINES[engine]), "tq_server_set_fp64_engine")
 
     def step_async(self):
         """Collect the previous tick, launch the next one, return at once:

@@ -170,6 +170,9 @@ void tc_test_limits(long long* max_tries, int* skip_mma);
 // tcgen05 tensor cores (tq_apply_oz.cu; a width-1 block runs as S (x) I);
 // needs n - 2 >= 4. S: the block's FP64 superoperator (4^w x 4^w).
 bool oz_eligible(int n, int width);
+// Whether an FP64 engine setting (tq_fp64_engine) means the tensor cores
+// (TQ_ENGINE_TENSOR, or TQ_ENGINE_AUTO where the library chooses them).
+bool fp64_engine_is_tensor(int engine);
 cudaError_t launch_herm_oz(double2* rho, const double2* S, const ApplyParams& p, int num_sms, cudaStream_t st);
 cudaError_t oz_take_timeouts(unsigned int* count, cudaStream_t st);
 

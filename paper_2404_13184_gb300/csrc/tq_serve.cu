@@ -67,6 +67,14 @@ class Arena {
   std::map<size_t, size_t> free_;
 };
 
+// Requests of at least this many qubits advance through the single-state
+// apply kernels, one launch per fused block, instead of the persistent
+// batch kernel: their passes are long (>= ~40 us) next to a launch, and the
+// single-state kernels run on the tensor cores (split width 2; FP64 widths
+// <= 2 with the tensor-core engine), closer to the HBM bound than the batch
+// kernel's CUDA-core tiles.
+constexpr int kDirectQubits = 12;
+
 struct Req {
   int n = 0;
   std::vector<unsigned long long> masks;
@@ -110,9 +118,18 @@ struct tq_server {
   size_t res_off = 0, err_off = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // GPU time of the pending tick
   double gpu_ms = 0.0;
+  int fp64_engine = TQ_ENGINE_AUTO;  // tq_server_set_fp64_engine
+  bool pend_direct_tc = false;       // the pending tick launched tensor-core passes
 };
 
 namespace {
+
+// Whether a live request of n qubits advances through single-state launches.
+bool direct_request(const tq_server* s, int n) {
+  if (n < kDirectQubits) return false;
+  if (s->prec == TQ_SPLIT) return true;
+  return fp64_engine_is_tensor(s->fp64_engine) && oz_eligible(n, 2);
+}
 
 tq_status st_of(cudaError_t e) {
   if (e == cudaSuccess) return TQ_OK;
@@ -146,6 +163,7 @@ cudaError_t grow_pin(PinBuf& b, size_t bytes) {
 }
 
 size_t entry_size(int prec) { return prec == TQ_FP64 ? 16 : 8; }
+
 
 // Blocks a live request advances per tick: about 8 passes of a 12-qubit
 // register's worth of entries, at least one block.
@@ -309,6 +327,14 @@ tq_status collect_tick(tq_server* s, int* n_finished) {
   const char* h = static_cast<const char*>(s->pin_res.ptr);
   int err_flag = 0;
   if (s->pend_items) std::memcpy(&err_flag, h + s->err_off, sizeof(int));
+  if (s->pend_direct_tc) {  // bounded waits of the tick's tensor-core passes
+    unsigned int a = 0, b = 0;
+    e = tc_take_timeouts(&a, s->stream);
+    if (e == cudaSuccess) e = oz_take_timeouts(&b, s->stream);
+    if (e != cudaSuccess) return st_of(e);
+    if (a || b) err_flag = 1;
+    s->pend_direct_tc = false;
+  }
   if (!s->pend_done.empty()) {
     const double* res = reinterpret_cast<const double*>(h + s->res_off);
     for (size_t k = 0; k < s->pend_done.size(); ++k) {
@@ -364,7 +390,7 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
   std::vector<int> job_req;
   std::vector<int> finishing;
   int max_cnt = 0;
-  std::vector<int> cnts;
+  std::vector<int> cnts, is_direct;
   for (int id : s->live) {
     Req& r = s->reqs[id];
     const int nb = (int)r.prog.params.size();
@@ -390,15 +416,17 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
       blks.push_back(bb);
     }
     set_tiles(blks.data() + j.block0, cnt, j.tile_log2, j.herm != 0, tiled16_job(r.n, s->prec));
-    if (cnt > 0 && j.resident) items.push_back(BItem{(int)jobs.size(), -1, 0, cnt});
+    const bool direct = direct_request(s, r.n);
+    if (cnt > 0 && j.resident && !direct) items.push_back(BItem{(int)jobs.size(), -1, 0, cnt});
     job_req.push_back(id);
     cnts.push_back(cnt);
-    if (!j.resident) max_cnt = std::max(max_cnt, cnt);
+    is_direct.push_back(direct ? 1 : 0);
+    if (!j.resident && !direct) max_cnt = std::max(max_cnt, cnt);
     jobs.push_back(j);
   }
   for (int k = 0; k < max_cnt; ++k)
     for (size_t j = 0; j < jobs.size(); ++j) {
-      if (jobs[j].resident || k >= cnts[j]) continue;
+      if (jobs[j].resident || is_direct[j] || k >= cnts[j]) continue;
       const int tiles = blks[jobs[j].block0 + k].tiles;
       for (int t = 0; t < tiles; ++t) items.push_back(BItem{(int)j, k, t, 1});
     }
@@ -436,6 +464,29 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
           ticket + 32, s->max_spin);
     e = cudaGetLastError();
     if (e != cudaSuccess) return st_of(e);
+  }
+  // 2b. large requests: their blocks as single-state launches (Hermitian
+  // mode, as in the batch kernel), after the batch kernel on the same stream
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    if (!is_direct[j]) continue;
+    char* rho = static_cast<char*>(s->rho_mem.ptr) + jobs[j].rho_off;
+    for (int k = 0; k < cnts[j]; ++k) {
+      const BBlk& bb = blks[jobs[j].block0 + k];
+      ApplyParams p = bb.p;
+      p.sparse = 0;
+      if (s->prec == TQ_FP64) {
+        e = launch_herm_oz(reinterpret_cast<double2*>(rho), static_cast<const double2*>(bb.S), p, s->num_sms,
+                           s->stream);
+        s->pend_direct_tc = true;
+      } else if (p.width == 2) {
+        e = launch_herm_tc2(reinterpret_cast<float2*>(rho), static_cast<const float2*>(bb.S), p, s->num_sms,
+                            s->stream);
+        s->pend_direct_tc = true;
+      } else {
+        e = launch_apply(rho, TQ_SPLIT, bb.S, p, s->num_sms, s->stream);
+      }
+      if (e != cudaSuccess) return st_of(e);
+    }
   }
   // 3. progress; readouts of the requests this tick finishes are reduced and
   // copied to the staging buffer behind the tick (collected later)
@@ -511,6 +562,12 @@ tq_status tq_server_step_async(tq_server* s, int* n_live, int* n_queued, int* n_
   tq_status st = collect_tick(s, n_finished);
   if (st != TQ_OK) return st;
   return launch_tick(s, n_live, n_queued);
+}
+
+tq_status tq_server_set_fp64_engine(tq_server* s, int engine) {
+  if (!s || engine < TQ_ENGINE_AUTO || engine > TQ_ENGINE_TENSOR) return TQ_ERR_ARG;
+  s->fp64_engine = engine;
+  return TQ_OK;
 }
 
 tq_status tq_server_gpu_ms(const tq_server* s, double* ms) {

@@ -168,9 +168,7 @@ void free_buf(DevBuf& b) {
 
 size_t entry_bytes(int prec) { return prec == TQ_FP64 ? 16 : 8; }
 
-bool fp64_on_tensor(const tq_state* s) {
-  return s->fp64_engine == TQ_ENGINE_TENSOR || (s->fp64_engine == TQ_ENGINE_AUTO && kAutoTensor);
-}
+bool fp64_on_tensor(const tq_state* s) { return fp64_engine_is_tensor(s->fp64_engine); }
 
 tq_status check_state(tq_state* s) {
   if (!s) return TQ_ERR_ARG;
@@ -243,6 +241,10 @@ void fold_pending(tq_state* s) {
 }  // namespace
 
 namespace tq {
+
+bool fp64_engine_is_tensor(int engine) {
+  return engine == TQ_ENGINE_TENSOR || (engine == TQ_ENGINE_AUTO && kAutoTensor);
+}
 
 ApplyParams apply_params(int n, const Block& B) {
   ApplyParams p{};

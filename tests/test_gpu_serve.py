@@ -174,3 +174,34 @@ def test_submit_rejects_tables_beyond_the_table_budget(tq):
     want = O.run_circuit(4, small.ops)
     assert st == 2 and abs(res[2] - O.expect_z(want, 1)) < TOL64
     srv.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_large_requests_run_through_single_state_kernels(tq, precision):
+    # requests of >= 12 qubits advance by single-state launches (tensor cores:
+    # split width 2, and FP64 with the tensor engine) after the tick's batch
+    # kernel, while small ones stay in it; every result must equal the
+    # request's single-state run (FP64: the DFMA engine, held to the oracle
+    # by the parity tests) within the precision's tolerance
+    rng = np.random.default_rng(41)
+    reqs = []
+    for n, depth in ((12, 12), (5, 40), (13, 6), (7, 30), (12, 10)):
+        c = W.served_request(rng, n_min=n, n_max=n, d_min=depth, d_max=depth)
+        reqs.append((n, c.ops, [1, 3, (1 << n) - 1]))
+    srv = tq.Server(precision, rho_budget=8 << 30, max_live=3, engine="tensor")
+    ids = [srv.submit(n, ops, width=-1, masks=m) for n, ops, m in reqs]
+    guard = 0
+    while any(srv.poll(i)[0] != 2 for i in ids) and guard < 5000:
+        srv.step_async()
+        guard += 1
+    srv.step()
+    tol = TOL64 if precision == "fp64" else 1e-6
+    for (n, ops, masks), rid in zip(reqs, ids):
+        st_, got = srv.poll(rid)
+        assert st_ == 2
+        with tq.State(n, precision, engine="dfma") as st:
+            st.run(ops, width=-1)
+            tr = st.trace()
+            want = np.concatenate([[tr.real, tr.imag], st.expect_z(masks)])
+        assert np.max(np.abs(got - want)) < tol, (n, np.max(np.abs(got - want)))
+    srv.free()
