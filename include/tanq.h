@@ -486,8 +486,9 @@ typedef enum {
   TQ_PIPE_DFMA = 0,        /* fma.rn.f64: 2 flops per FMA */
   TQ_PIPE_DMMA = 1,        /* mma.sync.m8n8k4.f64: 512 flops per warp instruction */
   TQ_PIPE_FFMA = 2,        /* fma.rn.f32: 2 flops per FMA */
-  TQ_PIPE_CVT_F64_S64 = 3, /* cvt.rn.f64.s64: 1 op per conversion */
-  TQ_PIPE_CVT_F64_F32 = 4  /* cvt.f64.f32: 1 op per conversion */
+  TQ_PIPE_CVT_F64_S64 = 3, /* cvt.rn.f64.s64: 1 op per conversion (each feeding the
+                              next of its chain through one integer op) */
+  TQ_PIPE_CVT_F64_F32 = 4  /* cvt.f64.f32: 1 op per conversion (chained likewise) */
 } tq_pipe;
 
 /* Run the probe of `pipe` on every SM of the current device (4 CTAs of 256

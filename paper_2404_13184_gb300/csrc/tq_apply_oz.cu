@@ -40,13 +40,15 @@
 //
 // Work unit, group walk and Hermitian bookkeeping follow the split
 // tensor-core kernel (tq_apply_tc.cu): half of a 16 x 16 tile of canonical
-// groups, one group per thread, a CTA of 128 threads. Per unit a thread
-// issues the loads of its next group's 16 entries into registers, slices the
-// current group into the eight digit operands (A_0..A_7, 8 KB each in shared
-// memory), and after a CTA barrier one thread issues the 72 MMAs (36 digit
-// pairs x two K-halves, M = 128, N = 32, K = 16) into 7 accumulators of 32
-// tensor-memory columns and commits them to an mbarrier; every thread waits
-// (bounded), reads its row of the accumulators and writes its 16 outputs.
+// groups (128 groups), with two threads per group in a CTA of 256 threads,
+// each taking 8 of the group's 16 entries and 8 of its 16 outputs. Per unit
+// a thread issues the loads of its next group half into registers, slices
+// its current half into the eight digit operands (A_0..A_7, 8 KB each in
+// shared memory), and after a CTA barrier one thread issues the 72 MMAs (36
+// digit pairs x two K-halves, M = 128, N = 32, K = 16) into 7 accumulators
+// of 32 tensor-memory columns and commits them to an mbarrier; every thread
+// waits (bounded), reads its part of its row of the accumulators and writes
+// its 8 outputs.
 //
 // Width-1 blocks run through the same kernel as a width-2 block with the
 // identity on a second qubit (S (x) I, built while slicing R), which moves
@@ -69,7 +71,7 @@ using namespace tc;
 // oz_take_timeouts().
 __device__ unsigned int g_oz_timeouts;
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // two threads per group of a 128-group unit
 constexpr int kTile = 16;
 constexpr int kDigits = 8;                          // 7-bit digits per operand value
 constexpr int kAccs = 7;                            // orders 0..5 exact, 6 and 7 shared
@@ -77,60 +79,64 @@ constexpr uint32_t kADigitBytes = 128 * kRowBytes;  // 128 groups x 32 BF16
 constexpr uint32_t kOffA = 0;
 constexpr uint32_t kOffB = kOffA + kDigits * kADigitBytes;
 constexpr uint32_t kOffG = kOffB + kDigits * kBTermBytes;  // 32 row exponents
-constexpr uint32_t kOffBar = kOffG + 32 * 4;
+constexpr uint32_t kOffE = kOffG + 32 * 4;                // 2 x 128 half maxima
+constexpr uint32_t kOffBar = kOffE + 256 * 4;
 constexpr uint32_t kOffTmem = kOffBar + 8;
 constexpr uint32_t kOffFlag = kOffTmem + 4;
 constexpr uint32_t kSmemBytes = kOffFlag + 4;
 constexpr uint32_t kTmemCols = 256;
 constexpr int kCtasPerSm = 2;
 
-// Digit i of a value whose 56-bit aligned magnitude is F, as the FP32 number
-// +-d_i 2^(-7 i): d_i is placed in mantissa bits 16..22 of a float of
-// exponent 2^(7 - 7 i) (with the value's sign) and that float's leading 1
-// is subtracted off (exact).
+// Digit I of the magnitude held in f's bits 16..22 (already shifted there),
+// as the FP32 number d_I 2^(-7 I): d_I is placed in mantissa bits 16..22 of
+// a float of exponent 2^(7 - 7 I) and that float's leading 1 is subtracted
+// off (exact; the sign is applied to the packed BF16 pair afterwards).
 template <int I>
-__device__ __forceinline__ float digit(unsigned long long F, uint32_t sgn) {
-  constexpr int sh = 33 - 7 * I;  // moves bits 49 - 7 I .. 55 - 7 I to 16 .. 22
-  const uint32_t f = sh >= 0 ? (uint32_t)(F >> (sh >= 0 ? sh : 0)) : (uint32_t)(F << (sh < 0 ? -sh : 0));
-  const uint32_t bias = ((uint32_t)(134 - 7 * I) << 23) | sgn;
+__device__ __forceinline__ float digit(uint32_t f) {
+  constexpr uint32_t bias = (uint32_t)(134 - 7 * I) << 23;
   return __uint_as_float((f & 0x7f0000u) | bias) - __uint_as_float(bias);
 }
 
-// The eight digits of v aligned to biased exponent E (v's exponent <= E):
-// the significand shifted right by E - e_v and rounded to nearest (ties
-// away from zero), so F < 2^56 and the alignment error is unbiased. Zeros
-// and subnormals (exponent field 0) give zero digits.
-__device__ __forceinline__ void digits8(double v, int E, float d[kDigits]) {
+// The eight digit magnitudes of v aligned to biased exponent E (v's exponent
+// <= E): the significand shifted right by E - e_v and rounded to nearest
+// (ties away from zero), F < 2^56, digit i = bits 49 - 7 i .. 55 - 7 i of F.
+// Zeros and subnormals (exponent field 0) give zero digits. *sgn: v's sign
+// bit (bit 31).
+__device__ __forceinline__ void digits8(double v, int E, float d[kDigits], uint32_t* sgn) {
   const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-  const uint32_t sgn = hi & 0x80000000u;
+  *sgn = hi & 0x80000000u;
   const int ev = (int)((hi >> 20) & 0x7ffu);
   const int sh = E - ev;
   const unsigned long long M3 = (((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) << 3;
   const unsigned long long F =
       (ev == 0 || sh > 56) ? 0ull : sh == 0 ? M3 : (((M3 >> (sh - 1)) + 1ull) >> 1);
-  d[0] = digit<0>(F, sgn);
-  d[1] = digit<1>(F, sgn);
-  d[2] = digit<2>(F, sgn);
-  d[3] = digit<3>(F, sgn);
-  d[4] = digit<4>(F, sgn);
-  d[5] = digit<5>(F, sgn);
-  d[6] = digit<6>(F, sgn);
-  d[7] = digit<7>(F, sgn);
+  const uint32_t fh = (uint32_t)(F >> 32), fl = (uint32_t)F;  // bits 32..55 and 0..31
+  d[0] = digit<0>(fh >> 1);                         // bits 49..55
+  d[1] = digit<1>(fh << 6);                         // 42..48
+  d[2] = digit<2>(fh << 13);                        // 35..41
+  d[3] = digit<3>(__funnelshift_r(fl, fh, 12));     // 28..34
+  d[4] = digit<4>(fl >> 5);                         // 21..27
+  d[5] = digit<5>(fl << 2);                         // 14..20
+  d[6] = digit<6>(fl << 9);                         // 7..13
+  d[7] = digit<7>(fl << 16);                        // 0..6
 }
 
 __device__ __forceinline__ uint32_t abs_hi(double v) { return (uint32_t)__double2hiint(v) & 0x7fffffffu; }
 
 // Stores the digit words of 4 consecutive complex entries (one 16-byte chunk
-// of every digit operand's row).
+// of every digit operand's row): BF16 pairs (Re digit, Im digit) with the
+// entries' signs.
 __device__ __forceinline__ void store_chunk(const double2 x[4], int E, uint32_t row_chunk, uint32_t digit_bytes) {
   uint32_t w[kDigits][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     float dr[kDigits], di[kDigits];
-    digits8(x[e].x, E, dr);
-    digits8(x[e].y, E, di);
+    uint32_t sr, si;
+    digits8(x[e].x, E, dr, &sr);
+    digits8(x[e].y, E, di, &si);
+    const uint32_t sign = (sr >> 16) | si;  // sign bits of the low and high BF16 halves
 #pragma unroll
-    for (int i = 0; i < kDigits; ++i) w[i][e] = pack_bf16x2(dr[i], di[i]);
+    for (int i = 0; i < kDigits; ++i) w[i][e] = pack_bf16x2(dr[i], di[i]) ^ sign;
   }
 #pragma unroll
   for (int i = 0; i < kDigits; ++i) sts128(row_chunk + i * digit_bytes, w[i][0], w[i][1], w[i][2], w[i][3]);
@@ -220,20 +226,45 @@ struct Group {
   bool active, self;
 };
 
+// Accumulator values of this thread's 8 real outputs n0 .. n0 + 7 (columns
+// n0.. of each of the 7 accumulators), all loads issued before one wait.
+__device__ __forceinline__ void load_accs(uint32_t t_row, int n0, uint32_t r[kAccs][8]) {
+#pragma unroll
+  for (int a = 0; a < kAccs; ++a)
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[a][0]), "=r"(r[a][1]), "=r"(r[a][2]), "=r"(r[a][3]), "=r"(r[a][4]), "=r"(r[a][5]),
+                   "=r"(r[a][6]), "=r"(r[a][7])
+                 : "r"(t_row + (uint32_t)(32 * a + n0))
+                 : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  // the values are read only after the wait
+#pragma unroll
+  for (int a = 0; a < kAccs; ++a)
+    asm volatile("" : "+r"(r[a][0]), "+r"(r[a][1]), "+r"(r[a][2]), "+r"(r[a][3]), "+r"(r[a][4]), "+r"(r[a][5]),
+                 "+r"(r[a][6]), "+r"(r[a][7]));
+}
+
+// Two threads per group: thread tid takes group row m = tid % 128 of the unit
+// (its A row and TMEM lane) and half h = tid / 128 of the group, the entries
+// and outputs 8 h .. 8 h + 7 (A chunks 2 h, 2 h + 1; accumulator columns
+// 16 h .. 16 h + 15). The group's alignment exponent is the larger of the two
+// halves' maxima, exchanged through shared memory.
 // max_tries: try_wait rounds before an MMA wait gives up; skip_mma (tests
 // of the failure path only): issue neither the MMAs nor their commit.
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2* rho, const double2* __restrict__ S,
                                                                            const __grid_constant__ ApplyParams p,
                                                                            int embed, long long max_tries,
                                                                            int skip_mma) {
-  constexpr int D = 16;
+  constexpr int H = 8;  // entries (and complex outputs) per thread
   extern __shared__ __align__(1024) unsigned char smem[];
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t bar = sbase + kOffBar;
   volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
   volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kOffFlag);
   const int* s_G = reinterpret_cast<const int*>(smem + kOffG);
+  uint32_t* s_E = reinterpret_cast<uint32_t*>(smem + kOffE);  // [2][128] half maxima
   const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  const int m = tid & 127, h = tid >> 7, wq = w & 3;
 
   int qs[2] = {p.q[0], p.q[1]};
   if (qs[0] > qs[1]) {
@@ -242,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     qs[1] = t;
   }
   const unsigned int b0 = 1u << p.q[0], b1 = 1u << p.q[1], N = 1u << p.n;
-  build_b_digits(smem, sbase, S, embed, tid);
+  if (tid < 128) build_b_digits(smem, sbase, S, embed, tid);
   if (tid == 0) {
     bar_init(bar, 1);
     *s_abort = 0;
@@ -254,12 +285,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
   fence_after_sync();
   const uint32_t tmem = *s_tmem;
 
-  // a warp covers 8 row rests x 4 column rests of the half tile
-  const int i = (lane % 8) + 8 * (w % 2), j0 = (lane / 8) + 4 * (w / 2);
+  // a warp quarter covers 8 row rests x 4 column rests of the half tile
+  const int i = (lane % 8) + 8 * (wq % 2), j0 = (lane / 8) + 4 * (wq / 2);
   const unsigned int di = (unsigned int)deposit_zeros(i, qs, 2), dj0 = (unsigned int)deposit_zeros(j0, qs, 2),
                      dj1 = (unsigned int)deposit_zeros(j0 + 8, qs, 2);
-  const uint32_t a_row = sbase + kOffA + core_off(tid, 0);
-  const uint32_t t_row = tmem + ((uint32_t)(32 * w) << 16);  // this warp's 32 TMEM lanes
+  const uint32_t a_row = sbase + kOffA + core_off(m, 2 * h);
+  const uint32_t t_row = tmem + ((uint32_t)(32 * wq) << 16);  // this warp's 32 TMEM lanes
   const unsigned long long Mt = (1ull << (p.n - 2)) / kTile;
   const unsigned long long n_units = Mt * (Mt + 1);
 
@@ -274,18 +305,20 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     g.cb = (unsigned int)deposit_zeros((tt >> 32) * kTile, qs, 2) + ((u & 1ull) ? dj1 : dj0);
     return g;
   };
-  auto load = [&](const Group& g, double2 x[D]) {
+  // this thread's half of the group: entries 8 h .. 8 h + 7 (stored copies;
+  // those read from their transposes are conjugated at use)
+  auto load = [&](const Group& g, double2 x[H]) {
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
+    for (int l = 0; l < H; ++l) {
       bool up;
-      const unsigned int idx = entry_index(g.rb, g.cb, l, b0, b1, N, &up);
+      const unsigned int idx = entry_index(g.rb, g.cb, H * h + l, b0, b1, N, &up);
       x[l] = g.active ? rho[idx] : make_double2(0.0, 0.0);
     }
   };
 
   unsigned long long u = blockIdx.x;
   Group gn{};
-  double2 xn[D];
+  double2 xn[H];
   if (u < n_units) {
     gn = group_of(u);
     load(gn, xn);
@@ -294,26 +327,26 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
 #pragma unroll 1
   for (; u < n_units; u += gridDim.x, phase ^= 1u) {
     const Group g = gn;
-    double2 x[D];
+    double2 x[H];
 #pragma unroll
-    for (int l = 0; l < D; ++l) x[l] = xn[l];
+    for (int l = 0; l < H; ++l) x[l] = xn[l];
     if (u + gridDim.x < n_units) {
       gn = group_of(u + gridDim.x);
       load(gn, xn);
     }
-    // entries read from their transposes are conjugated; the group's
-    // alignment is its largest exponent
     uint32_t mx = 0;
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
+    for (int l = 0; l < H; ++l) {
       bool up;
-      (void)entry_index(g.rb, g.cb, l, b0, b1, N, &up);
+      (void)entry_index(g.rb, g.cb, H * h + l, b0, b1, N, &up);
       if (!up) x[l].y = -x[l].y;
       mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
     }
-    const int E = (int)(mx >> 20);
+    s_E[tid] = mx;
+    __syncthreads();  // both halves' maxima (and the previous unit's TMEM reads are done)
+    const int E = (int)(max(mx, s_E[tid ^ 128]) >> 20);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) store_chunk(x + 4 * c, E, a_row + c * 128u, kADigitBytes);
+    for (int c = 0; c < 2; ++c) store_chunk(x + 4 * c, E, a_row + c * 128u, kADigitBytes);
     fence_operands();
     fence_before_sync();
     __syncthreads();
@@ -323,10 +356,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
       // accumulator a <- the digit pairs of order t = a (a < 6); accumulator
       // 6 <- order 7, then order 6 (smallest first). The first MMA of each
       // accumulator overwrites it.
-      const int order_of[8] = {0, 1, 2, 3, 4, 5, 7, 6};
 #pragma unroll 1
       for (int s = 0; s < 8; ++s) {
-        const int t = order_of[s];
+        const int t = s < 6 ? s : 13 - s;  // 0, 1, 2, 3, 4, 5, 7, 6
         const uint32_t d_acc = tmem + (uint32_t)(32 * (t < 6 ? t : 6));
 #pragma unroll 1
         for (int ia = 0; ia <= t; ++ia) {  // digit ia of x times digit t - ia of R (t <= 7 < kDigits)
@@ -350,19 +382,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     if (!__all_sync(0xffffffffu, waited)) continue;
     fence_after_sync();
 #pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {  // 8 real outputs (4 entries) per chunk
-      float cv[kAccs][8];
-#pragma unroll
-      for (int a = 0; a < kAccs; ++a) tmem_ld8(t_row + (uint32_t)(32 * a + 8 * ch), cv[a]);
+    for (int ch = 0; ch < 2; ++ch) {  // 8 real outputs (4 entries) per chunk
+      uint32_t cv[kAccs][8];
+      load_accs(t_row, 16 * h + 8 * ch, cv);
       if (!g.active) continue;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int o = 4 * ch + e;
+        const int o = H * h + 4 * ch + e;
         float cr[kAccs], ci[kAccs];
 #pragma unroll
         for (int a = 0; a < kAccs; ++a) {
-          cr[a] = cv[a][2 * e];
-          ci[a] = cv[a][2 * e + 1];
+          cr[a] = __uint_as_float(cv[a][2 * e]);
+          ci[a] = __uint_as_float(cv[a][2 * e + 1]);
         }
         double2 y;
         y.x = recombine(cr, E + s_G[2 * o] - 2100);

@@ -74,44 +74,46 @@ __global__ void __launch_bounds__(256) k_probe_dmma(double* out, int iters, doub
 }
 
 // Conversions: 64-bit integer -> FP64 (cvt.rn.f64.s64) and FP32 -> FP64
+// (cvt.f64.f32). Each conversion's result feeds the next one of its chain
+// (its bit pattern reinterpreted, one integer op), so none can be dropped.
 __global__ void __launch_bounds__(256) k_probe_cvt_s64(double* out, int iters, long long seed) {
   long long v[kChains];
-  double r[kChains];
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) {
-    v[c] = seed + threadIdx.x * 977 + c;
-    r[c] = 0.0;
-  }
+  for (int c = 0; c < kChains; ++c) v[c] = seed + threadIdx.x * 977 + c;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-      for (int c = 0; c < kChains; ++c) asm volatile("cvt.rn.f64.s64 %0, %1;" : "=d"(r[c]) : "l"(v[c] + u));
+      for (int c = 0; c < kChains; ++c) {
+        double r;
+        asm volatile("cvt.rn.f64.s64 %0, %1;" : "=d"(r) : "l"(v[c]));
+        v[c] = __double_as_longlong(r) >> 12;  // a 52-bit integer again
+      }
   }
-  double s = 0.0;
+  long long s = 0;
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) s += r[c];
-  if (s == 12345.678) out[0] = s;
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  if (s == 12345) out[0] = (double)s;
 }
 
 __global__ void __launch_bounds__(256) k_probe_cvt_f32(double* out, int iters, float seed) {
   float v[kChains];
-  double r[kChains];
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) {
-    v[c] = seed + threadIdx.x + c;
-    r[c] = 0.0;
-  }
+  for (int c = 0; c < kChains; ++c) v[c] = seed + threadIdx.x + c;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-      for (int c = 0; c < kChains; ++c) asm volatile("cvt.f64.f32 %0, %1;" : "=d"(r[c]) : "f"(v[c]));
+      for (int c = 0; c < kChains; ++c) {
+        double r;
+        asm volatile("cvt.f64.f32 %0, %1;" : "=d"(r) : "f"(v[c]));
+        v[c] = __int_as_float(__double2hiint(r) | 0x3f800000);  // a float in [1, 2) again
+      }
   }
-  double s = 0.0;
+  float s = 0.f;
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) s += r[c];
-  if (s == 12345.678) out[0] = s;
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  if (s == 12345.678f) out[0] = s;
 }
 
 }  // namespace
