@@ -23,20 +23,24 @@
 // P_t an integer with |P_t| <= (t + 1) * 32 * 127^2 < 2^22 for t <= 7: every
 // partial sum of an order is an integer multiple of 2^(-7 t) below 2^22 of
 // those units, so FP32 accumulation in tensor memory is EXACT for each
-// order. Orders 0..5 get an accumulator each; orders 6 and 7 (weight <=
-// 2^-42 of order 0) share one, whose FP32 roundings are ~2^-58 of the
-// largest term; orders >= 8 (~2^-53) are dropped.
+// order. Each order 0..7 has its own accumulator of 32 columns; orders >= 8
+// (~2^-53 of order 0) are dropped. The B operand holds the digit slabs
+// B_0..B_7 one after another along N, so ONE MMA of A digit i against
+// B_0..B_(7-i) (N = 32 (8 - i)) adds the products of every order i + j to
+// the consecutive accumulator blocks i..7: 8 MMAs per K-half instead of one
+// per digit pair.
 //
-// Recombination without FP64 arithmetic: each exact accumulator becomes its
-// integer by one FP32 add of 1.5 * 2^(23 - 7 t) (the float's low mantissa
-// bits then hold P_t); the shared accumulator is rounded to units of 2^-42
-// the same way. The integers are combined into one 64-bit integer Z (in
-// units of 2^-42 of C_0; |Z| < 2^62) with wide integer multiply-adds, Z is
-// converted to FP64 (one rounding) and scaled by adding E_m + G_n - 2100 to
-// its exponent field. Per real output that is one conversion and no FP64
-// multiply or add; the result is FP64-accurate relative to the group's
-// largest entry (rounding of the operands at 2^-57 of their alignment,
-// ~2^-53 from the dropped orders, one final rounding).
+// Recombination without FP64 arithmetic: each accumulator of orders 0..6
+// becomes its integer by one FP32 add of 1.5 * 2^(23 - 7 t) (the float's low
+// mantissa bits then hold P_t); order 7 is rounded to units of 2^-42 the
+// same way. The integers are combined into one 64-bit integer Z (in units
+// of 2^-42 of C_0; |Z| < 2^62) with wide integer multiply-adds, and Z is
+// converted to FP64 with integer operations only (leading-zero count,
+// shift, round to nearest with ties away from zero, exponent E_m + G_n -
+// 2100 + 1023 placed directly): no FP64 instruction at all. The result is
+// FP64-accurate relative to the group's largest entry (rounding of the
+// operands at 2^-57 of their alignment, ~2^-53 from the dropped orders and
+// order 7's rounding, one final rounding).
 //
 // Work unit, group walk and Hermitian bookkeeping follow the split
 // tensor-core kernel (tq_apply_tc.cu): half of a 16 x 16 tile of canonical
@@ -44,8 +48,7 @@
 // each taking 8 of the group's 16 entries and 8 of its 16 outputs. Per unit
 // a thread issues the loads of its next group half into registers, slices
 // its current half into the eight digit operands (A_0..A_7, 8 KB each in
-// shared memory), and after a CTA barrier one thread issues the 72 MMAs (36
-// digit pairs x two K-halves, M = 128, N = 32, K = 16) into 7 accumulators
+// shared memory), and after a CTA barrier one thread issues the 16 MMAs (8 pairs x two K-halves, M = 128, N = 32, K = 16) into 7 accumulators
 // of 32 tensor-memory columns and commits them to an mbarrier; every thread
 // waits (bounded), reads its part of its row of the accumulators and writes
 // its 8 outputs.
@@ -74,7 +77,7 @@ __device__ unsigned int g_oz_timeouts;
 constexpr int kThreads = 256;  // two threads per group of a 128-group unit
 constexpr int kTile = 16;
 constexpr int kDigits = 8;                          // 7-bit digits per operand value
-constexpr int kAccs = 7;                            // orders 0..5 exact, 6 and 7 shared
+constexpr int kAccs = 8;                            // one accumulator per order 0..7
 constexpr uint32_t kADigitBytes = 128 * kRowBytes;  // 128 groups x 32 BF16
 constexpr uint32_t kOffA = 0;
 constexpr uint32_t kOffB = kOffA + kDigits * kADigitBytes;
@@ -187,17 +190,18 @@ __device__ __forceinline__ unsigned long long mad_wide(uint32_t a, uint32_t b, u
 __host__ __device__ constexpr uint32_t magic_bits(int u) { return ((uint32_t)(150 - u) << 23) | 0x400000u; }
 
 // sum over the accumulators of the magic patterns at their weights (mod
-// 2^64), subtracted once from the combined raw patterns
+// 2^64), subtracted once from the combined raw patterns (orders 6 and 7 both
+// in units of 2^-42)
 __host__ __device__ constexpr unsigned long long magic_offset() {
   return ((unsigned long long)magic_bits(0) << 42) + ((unsigned long long)magic_bits(7) << 35) +
          ((unsigned long long)magic_bits(14) << 28) + ((unsigned long long)magic_bits(21) << 21) +
          ((unsigned long long)magic_bits(28) << 14) + ((unsigned long long)magic_bits(35) << 7) +
-         (unsigned long long)magic_bits(42);
+         2ull * (unsigned long long)magic_bits(42);
 }
 
-// Real output from its 7 accumulator values (orders 0..5, then 6 + 7): the
-// exact integer sum in units of 2^-42 of order 0, converted and scaled by
-// 2^(E + G - 2100).
+// Real output from its 8 accumulator values (orders 0..7): Z, their sum in
+// integer units of 2^-42 of order 0, as the FP64 number Z * 2^scale (scale =
+// E + G - 2100), built from Z's bits with integer operations.
 __device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
   const uint32_t b0 = __float_as_uint(c[0] + __uint_as_float(magic_bits(0)));
   const uint32_t b1 = __float_as_uint(c[1] + __uint_as_float(magic_bits(7)));
@@ -205,20 +209,27 @@ __device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
   const uint32_t b3 = __float_as_uint(c[3] + __uint_as_float(magic_bits(21)));
   const uint32_t b4 = __float_as_uint(c[4] + __uint_as_float(magic_bits(28)));
   const uint32_t b5 = __float_as_uint(c[5] + __uint_as_float(magic_bits(35)));
-  const uint32_t bq = __float_as_uint(c[6] + __uint_as_float(magic_bits(42)));
+  const uint32_t b6 = __float_as_uint(c[6] + __uint_as_float(magic_bits(42)));
+  const uint32_t b7 = __float_as_uint(c[7] + __uint_as_float(magic_bits(42)));  // rounded to 2^-42
   unsigned long long Z = (unsigned long long)(b0 * 128u + b1) << 35;  // wraps mod 2^64 like the rest
   Z = mad_wide(b2, 1u << 28, Z);
   Z = mad_wide(b3, 1u << 21, Z);
   Z = mad_wide(b4, 1u << 14, Z);
   Z = mad_wide(b5, 1u << 7, Z);
-  Z += bq;
+  Z += (unsigned long long)b6 + b7;
   Z -= magic_offset();
-  double dz;
-  asm("cvt.rn.f64.s64 %0, %1;" : "=d"(dz) : "l"((long long)Z));
-  const uint32_t zh = (uint32_t)__double2hiint(dz);
-  const int ez = (int)((zh >> 20) & 0x7ffu);
-  if (ez == 0 || ez + scale <= 0) return 0.0;  // zero, or below the normal range (|y| < 2^-1022)
-  return __hiloint2double((int)(zh + ((uint32_t)scale << 20)), __double2loint(dz));
+  // |Z| normalised to bit 63, rounded to 53 bits (a carry into bit 53 lands
+  // in the exponent field), placed under the biased exponent 1086 - lz +
+  // scale; zero and results below the normal range give 0
+  const unsigned long long sm = (unsigned long long)((long long)Z >> 63);
+  unsigned long long a = (Z ^ sm) - sm;
+  if (a == 0ull) return 0.0;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  const unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);
+  const int eb = 1085 - lz + scale;  // biased exponent - 1 (mant carries the leading 1)
+  if (eb < 0) return 0.0;
+  return __longlong_as_double((long long)((sm & 0x8000000000000000ull) + ((unsigned long long)eb << 52) + mant));
 }
 
 struct Group {
@@ -273,6 +284,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     qs[1] = t;
   }
   const unsigned int b0 = 1u << p.q[0], b1 = 1u << p.q[1], N = 1u << p.n;
+  const unsigned int ch1 = h ? b1 : 0u;  // column target bit of this half's entries (local bit 3)
   if (tid < 128) build_b_digits(smem, sbase, S, embed, tid);
   if (tid == 0) {
     bar_init(bar, 1);
@@ -284,6 +296,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *s_tmem;
+  // operand descriptors of A_0 and B_0 (the shared window is below 256 KB, so
+  // adding an offset >> 4 to the start-address field never carries out of it)
+  const uint64_t a_desc0 = smem_desc(sbase + kOffA), b_desc0 = smem_desc(sbase + kOffB);
 
   // a warp quarter covers 8 row rests x 4 column rests of the half tile
   const int i = (lane % 8) + 8 * (wq % 2), j0 = (lane / 8) + 4 * (wq / 2);
@@ -302,16 +317,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     g.active = !(diag && i > j);
     g.self = diag && i == j;
     g.rb = (unsigned int)deposit_zeros((tt & 0xffffffffull) * kTile, qs, 2) + di;
-    g.cb = (unsigned int)deposit_zeros((tt >> 32) * kTile, qs, 2) + ((u & 1ull) ? dj1 : dj0);
+    g.cb = (unsigned int)deposit_zeros((tt >> 32) * kTile, qs, 2) + ((u & 1ull) ? dj1 : dj0) + ch1;
     return g;
   };
-  // this thread's half of the group: entries 8 h .. 8 h + 7 (stored copies;
+  // this thread's half of the group: entries 8 h .. 8 h + 7, i.e. local
+  // entries l < 8 from a column base that includes bit 3 (stored copies;
   // those read from their transposes are conjugated at use)
   auto load = [&](const Group& g, double2 x[H]) {
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       bool up;
-      const unsigned int idx = entry_index(g.rb, g.cb, H * h + l, b0, b1, N, &up);
+      const unsigned int idx = entry_index(g.rb, g.cb, l, b0, b1, N, &up);
       x[l] = g.active ? rho[idx] : make_double2(0.0, 0.0);
     }
   };
@@ -338,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       bool up;
-      (void)entry_index(g.rb, g.cb, H * h + l, b0, b1, N, &up);
+      (void)entry_index(g.rb, g.cb, l, b0, b1, N, &up);
       if (!up) x[l].y = -x[l].y;
       mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
     }
@@ -353,22 +369,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     if (*s_abort) break;
     if (tid == 0 && !skip_mma) {
       fence_after_sync();
-      // accumulator a <- the digit pairs of order t = a (a < 6); accumulator
-      // 6 <- order 7, then order 6 (smallest first). The first MMA of each
-      // accumulator overwrites it.
-#pragma unroll 1
-      for (int s = 0; s < 8; ++s) {
-        const int t = s < 6 ? s : 13 - s;  // 0, 1, 2, 3, 4, 5, 7, 6
-        const uint32_t d_acc = tmem + (uint32_t)(32 * (t < 6 ? t : 6));
-#pragma unroll 1
-        for (int ia = 0; ia <= t; ++ia) {  // digit ia of x times digit t - ia of R (t <= 7 < kDigits)
+      // A digit i against the stacked B_0 .. B_(7-i) (N = 32 (8 - i)) adds
+      // its products of orders i .. 7 to accumulator blocks i .. 7; the
+      // first MMA (digit 0, N = 256) overwrites every block
 #pragma unroll
-          for (int kh = 0; kh < 2; ++kh)
-            mma_bf16(d_acc, smem_desc(sbase + kOffA + ia * kADigitBytes + kh * 256),
-                     smem_desc(sbase + kOffB + (t - ia) * kBTermBytes + kh * 256),
-                     (s != 7 && ia == 0 && kh == 0) ? 0u : 1u);
-        }
-      }
+      for (int ia = 0; ia < kDigits; ++ia)
+#pragma unroll
+        for (int kh = 0; kh < 2; ++kh)
+          mma_bf16_n(tmem + (uint32_t)(32 * ia), a_desc0 + (uint64_t)((ia * kADigitBytes + kh * 256) >> 4),
+                     b_desc0 + (uint64_t)((kh * 256) >> 4), idesc_m128(32 * (kDigits - ia)),
+                     (ia == 0 && kh == 0) ? 0u : 1u);
       commit(bar);
     }
     const bool waited = bar_wait(bar, phase, max_tries);
@@ -399,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
         y.x = recombine(cr, E + s_G[2 * o] - 2100);
         y.y = recombine(ci, E + s_G[2 * o + 1] - 2100);
         bool up;
-        const unsigned int idx = entry_index(g.rb, g.cb, o, b0, b1, N, &up);
+        const unsigned int idx = entry_index(g.rb, g.cb, 4 * ch + e, b0, b1, N, &up);
         if (up) {
           rho[idx] = y;
         } else if (!g.self) {  // a self-conjugate group writes its upper entries only

@@ -85,6 +85,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
+// M = 128 and N = n (a multiple of 16, 16 .. 256).
+__host__ __device__ constexpr uint32_t idesc_m128(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // The 12 MMAs of one set of 128 operand rows: products (A_ta, B_tb) with
 // ta + tb <= 2, smallest first, two K-halves of 16 each, into the 32
 // accumulator columns at d_tmem. a0 / b0: shared addresses of term 0 of A

@@ -2,11 +2,11 @@
 (csrc/tq_apply_oz.cu), emulated bit by bit in numpy: every FP64 operand cut
 into eight 7-bit digits of a 56-bit fixed-point number aligned to the largest
 exponent of its group (inputs) or row (superoperator), the digit products
-summed per order t = i + j (orders 0..5 exactly, orders 6 and 7 in one FP32
-accumulator with one rounding per MMA), each accumulator turned into its
-integer by the 1.5 * 2^(23 - u) float addition, the integers combined in
-wrapped 64-bit arithmetic, converted to FP64 and scaled through the exponent
-field. The exact reference is the dot product in rational arithmetic. These
+summed exactly per order t = i + j (orders 0..7, each in its own FP32
+accumulator), each accumulator turned into its integer by the
+1.5 * 2^(23 - u) float addition (order 7 rounded to units of 2^-42), the
+integers combined in wrapped 64-bit arithmetic and converted to FP64 with
+integer operations only, the exponent placed directly. The exact reference is the dot product in rational arithmetic. These
 pin the digit layout, the orders, the magic constants and the scaling; the GPU
 tests hold the kernel itself to the oracle."""
 from fractions import Fraction
@@ -49,29 +49,44 @@ def magic_bits(u):
     return ((150 - u) << 23) | 0x400000
 
 
-def recombine(c, scale):
-    """c: 7 float32 accumulator values (orders 0..5, then 6 + 7)."""
-    bits = []
-    for a, u in zip(c, (0, 7, 14, 21, 28, 35, 42)):
-        f = np.float32(np.float32(a) + np.array([magic_bits(u)], dtype=np.uint32).view(np.float32)[0])
-        bits.append(int(np.array([f], dtype=np.float32).view(np.uint32)[0]))
-    b0, b1, b2, b3, b4, b5, bq = bits
-    Z = (((b0 * 128 + b1) & 0xFFFFFFFF) << 35) & MASK64
-    Z = (Z + b2 * (1 << 28)) & MASK64
-    Z = (Z + b3 * (1 << 21)) & MASK64
-    Z = (Z + b4 * (1 << 14)) & MASK64
-    Z = (Z + b5 * (1 << 7)) & MASK64
-    Z = (Z + bq) & MASK64
-    K = ((magic_bits(0) << 42) + (magic_bits(7) << 35) + (magic_bits(14) << 28) + (magic_bits(21) << 21)
-         + (magic_bits(28) << 14) + (magic_bits(35) << 7) + magic_bits(42)) & MASK64
-    Z = (Z - K) & MASK64
+def magic_int(a, u):
+    """The float32 bit pattern of a + 1.5 * 2^(23 - u) (one float32 addition)."""
+    f = np.float32(np.float32(a) + np.array([magic_bits(u)], dtype=np.uint32).view(np.float32)[0])
+    return int(np.array([f], dtype=np.float32).view(np.uint32)[0])
+
+
+def int_to_f64_scaled(Z, scale):
+    """The kernel's integer-only conversion of a two's-complement 64-bit Z to
+    FP64 times 2^scale: normalise |Z|, round to 53 bits (ties away from
+    zero), place the exponent 1086 - lz + scale; 0 for Z = 0 or below the
+    normal range."""
     Zs = Z - (1 << 64) if Z >> 63 else Z
-    dz = float(Zs)                                       # one rounding to nearest
-    s, ez, frac = fields(dz)
-    if ez == 0 or ez + scale <= 0:
+    if Zs == 0:
         return 0.0
-    b = (s << 63) | ((ez + scale) << 52) | frac
+    a = abs(Zs)
+    lz = 64 - a.bit_length()
+    a = (a << lz) & MASK64
+    mant = (a >> 11) + ((a >> 10) & 1)
+    eb = 1085 - lz + scale
+    if eb < 0:
+        return 0.0
+    b = ((1 << 63) if Zs < 0 else 0) + (eb << 52) + mant
     return float(np.array([b], dtype=np.uint64).view(np.float64)[0])
+
+
+def recombine(c, scale):
+    """c: 8 float32 accumulator values, orders 0..7."""
+    b = [magic_int(a, u) for a, u in zip(c[:7], (0, 7, 14, 21, 28, 35, 42))]
+    b.append(magic_int(c[7], 42))                        # order 7 rounded to units of 2^-42
+    Z = (((b[0] * 128 + b[1]) & 0xFFFFFFFF) << 35) & MASK64
+    Z = (Z + b[2] * (1 << 28)) & MASK64
+    Z = (Z + b[3] * (1 << 21)) & MASK64
+    Z = (Z + b[4] * (1 << 14)) & MASK64
+    Z = (Z + b[5] * (1 << 7)) & MASK64
+    Z = (Z + b[6] + b[7]) & MASK64
+    K = ((magic_bits(0) << 42) + (magic_bits(7) << 35) + (magic_bits(14) << 28) + (magic_bits(21) << 21)
+         + (magic_bits(28) << 14) + (magic_bits(35) << 7) + 2 * magic_bits(42)) & MASK64
+    return int_to_f64_scaled((Z - K) & MASK64, scale)
 
 
 def oz_dot(x, R_row):
@@ -80,19 +95,12 @@ def oz_dot(x, R_row):
     A = np.array([digits8(float(v), E) for v in x])      # [k][i]
     B = np.array([digits8(float(v), G) for v in R_row])  # [k][j]
     c = []
-    for t in range(6):                                   # exact orders, summed in float64 (exact here)
+    for t in range(8):                                   # every order exact (summed in float64, exact here)
         acc = 0.0
         for i in range(t + 1):
             acc += float(np.dot(A[:, i].astype(np.float64), B[:, t - i].astype(np.float64)))
         assert float(np.float32(acc)) == acc             # representable: FP32 accumulation is exact
         c.append(np.float32(acc))
-    acc = np.float32(0.0)                                # orders 7 then 6, one FP32 rounding per MMA
-    for t in (7, 6):
-        for i in range(t + 1):
-            for kh in (slice(0, 16), slice(16, 32)):
-                part = float(np.dot(A[kh, i].astype(np.float64), B[kh, t - i].astype(np.float64)))
-                acc = np.float32(float(acc) + part)
-    c.append(acc)
     return recombine(c, E + G - 2100), E, G
 
 
@@ -163,3 +171,18 @@ def test_signs_and_an_identity_row():
         e[k] = -1.0
         y, _, _ = oz_dot(x, e)
         assert abs(y + x[k]) <= 2.0 ** -52 * align(max_exp(x))
+
+
+def test_integer_conversion_rounds_to_nearest():
+    rng = np.random.default_rng(5)
+    for _ in range(5000):
+        z = int(rng.integers(-(1 << 62), 1 << 62))
+        s = int(rng.integers(-60, 60))
+        got = int_to_f64_scaled(z & MASK64, s)
+        want = Fraction(z) * Fraction(2) ** s
+        # within half a unit in the last place of the result
+        assert abs(Fraction(got) - want) <= abs(want) * Fraction(1, 2 ** 53)
+    assert int_to_f64_scaled(0, 5) == 0.0
+    assert int_to_f64_scaled((1 << 53) + 1, 0) == float((1 << 53) + 2)   # a tie rounds away from zero
+    assert int_to_f64_scaled((-(1 << 53) - 1) & MASK64, 0) == -float((1 << 53) + 2)
+    assert int_to_f64_scaled(1, -1075) == 0.0                             # below the normal range
