@@ -71,7 +71,7 @@ tq_status resolve_op(const tq_op& op, ResolvedOp* out);
 constexpr int kPlanF64Tensor = 16;
 // Relative pass time of the tensor-core FP64 engine against an HBM-bound
 // pass at the copy bandwidth (measured on GB300).
-constexpr double kTensorF64PassFactor = 1.5;
+constexpr double kTensorF64PassFactor = 2.9;
 
 // Per-precision cost (arbitrary units per 4^n entries) of one apply pass of
 // a block of the given width; nnz < 0 means dense. Used by the automatic

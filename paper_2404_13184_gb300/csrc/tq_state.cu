@@ -31,7 +31,7 @@ const char* kKindName[K_NKINDS] = {"superop_build", "fuse",         "reduce",   
 
 // Whether FP64 passes of widths <= 2 run on the tensor cores when the
 // engine is TQ_ENGINE_AUTO.
-constexpr bool kAutoTensor = false;
+constexpr bool kAutoTensor = true;
 
 struct Pending {
   int kind;

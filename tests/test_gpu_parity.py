@@ -88,13 +88,14 @@ def test_plain_6q_unfused_matches_oracle(tq):
         assert abs(zs[q] - O.expect_z(want, 1 << q)) < TOL64
 
 
+@pytest.mark.parametrize("engine", ["auto", "dfma"])
 @pytest.mark.parametrize("width", [0, 1, 2, 3, 4, -1])
 @pytest.mark.parametrize("n", [4, 5, 8])
-def test_fused_circuits_match_oracle_fp64(tq, n, width):
+def test_fused_circuits_match_oracle_fp64(tq, n, width, engine):
     c = W.random_noisy_circuit(n, 60, 40 + n, gate_set=("h", "s", "rz", "cx", "su2", "rzz"))
     c.ops += [("thermal", [0, n - 1], (300e-9, 100e-6, 80e-6)), ("pd", [n // 2], (0.05,))]
     want = O.run_circuit(n, c.ops)
-    with tq.State(n, "fp64") as st:
+    with tq.State(n, "fp64", engine=engine) as st:
         st.run(c.ops, width=width)
         got = st.rho()
     assert maxabs(got, want) < TOL64
@@ -253,14 +254,16 @@ def _factorised_check(tq, n, subset, width, precision, n_gates, seed, n_samples=
     assert err < tol, err
 
 
+@pytest.mark.parametrize("engine", ["auto", "dfma"])
 @pytest.mark.parametrize("width", [0, 1, 2, 3, 4])
-def test_full_size_12q_factorised(tq, width):
-    _factorised_check(tq, 12, [0, 5, 10, 11], width, "fp64", 40, 12)
+def test_full_size_12q_factorised(tq, width, engine):
+    _factorised_check(tq, 12, [0, 5, 10, 11], width, "fp64", 40, 12, engine=engine)
 
 
 def test_full_size_15q_factorised_fp64(tq):
-    # the 15-qubit register in the launch configuration of the benchmark
-    _factorised_check(tq, 15, [0, 6, 13, 14], -1, "fp64", 12, 15)
+    # the 15-qubit register in the launch configuration of the benchmark, on
+    # the DFMA engine (the tensor-core engine has its own checks)
+    _factorised_check(tq, 15, [0, 6, 13, 14], -1, "fp64", 12, 15, engine="dfma")
 
 
 def test_full_size_15q_factorised_split(tq):
@@ -268,8 +271,8 @@ def test_full_size_15q_factorised_split(tq):
 
 
 def test_max_size_16q_factorised_fp64(tq):
-    # the largest register (vec(rho) = 64 GiB in FP64; vec indices up to 2^32 - 1)
-    _factorised_check(tq, 16, [0, 7, 14, 15], -1, "fp64", 10, 17)
+    # the largest register (vec(rho) = 64 GiB in FP64; vec indices up to 2^32 - 1), DFMA engine
+    _factorised_check(tq, 16, [0, 7, 14, 15], -1, "fp64", 10, 17, engine="dfma")
 
 
 def test_max_size_16q_factorised_split(tq):
