@@ -10,37 +10,40 @@
 // 32 real inputs (Re, Im of the 16 entries, interleaved) and n one of the 32
 // real outputs.
 //
-// Fixed-point slicing. Every operand value is cut into eight 7-bit digits
-// of a 56-bit fixed-point number aligned to a shared exponent: for group m
+// Fixed-point slicing. Every operand value is cut into seven balanced 8-bit
+// digits of a fixed-point number aligned to a shared exponent: for group m
 // the largest biased exponent E_m of its 32 values, for output row n of R
 // the largest biased exponent G_n of the row. With F the value's 53-bit
-// significand shifted to that alignment (rounded to nearest, 56 bits),
-//     |v| ~ F * 2^(E - 1078),  F = sum_i d_i 2^(49 - 7 i),  0 <= d_i < 128,
-// and the BF16 operand of digit i is +-d_i 2^(-7 i) (exact: 7 significant
-// bits). Then
-//     Y[m][n] ~ 2^(E_m + G_n - 2100 + 42) sum_t C_t,
-//     C_t = sum_{i + j = t} sum_k A_i[m][k] B_j[n][k] = 2^(-7 t) P_t,
-// P_t an integer with |P_t| <= (t + 1) * 32 * 127^2 < 2^22 for t <= 7: every
-// partial sum of an order is an integer multiple of 2^(-7 t) below 2^22 of
-// those units, so FP32 accumulation in tensor memory is EXACT for each
-// order. Each order 0..7 has its own accumulator of 32 columns; orders >= 8
-// (~2^-53 of order 0) are dropped. The B operand holds the digit slabs
-// B_0..B_7 one after another along N, so ONE MMA of A digit i against
-// B_0..B_(7-i) (N = 32 (8 - i)) adds the products of every order i + j to
-// the consecutive accumulator blocks i..7: 8 MMAs per K-half instead of one
-// per digit pair.
+// significand shifted to that alignment and rounded to nearest (54 bits,
+// F < 2^54),
+//     |v| ~ F * 2^(E - 1076),   F = sum_i d_i 2^(8 (6 - i)),  -128 <= d_i < 128,
+// where the balanced digits come from the bytes of F + 0x0080808080808080
+// minus 128 (the added 128s carry exactly where a byte is >= 128; the top
+// byte stays below 192, so nothing is lost). A digit is an integer, exact in
+// FP16, and enters the tensor cores as such (the value's sign applied to
+// all its digits). Then
+//     Y[m][n] ~ 2^(E_m + G_n - 2152) sum_t 2^(8 (12 - t)) P_t,
+//     P_t = sum_{i + j = t} sum_k A_i[m][k] B_j[n][k],
+// P_t an integer with |P_t| <= 7 * 32 * 128^2 < 2^22: every partial sum is
+// an integer below 2^22, so FP32 accumulation in tensor memory is EXACT for
+// each order. Orders 0..7 have an accumulator of 32 columns each; orders
+// >= 8 (~2^-53 of order 0) are dropped. The B operand holds the digit slabs
+// B_0..B_6, and a zero slab B_7, one after another along N, so ONE MMA of A
+// digit i against B_0..B_(7-i) (N = 32 (8 - i); digit 0 against all eight,
+// which also clears block 7) adds the products of every order i + j to the
+// consecutive accumulator blocks i..7: 7 MMAs per K-half.
 //
-// Recombination without FP64 arithmetic: each accumulator of orders 0..6
-// becomes its integer by one FP32 add of 1.5 * 2^(23 - 7 t) (the float's low
-// mantissa bits then hold P_t); order 7 is rounded to units of 2^-42 the
-// same way. The integers are combined into one 64-bit integer Z (in units
-// of 2^-42 of C_0; |Z| < 2^62) with wide integer multiply-adds, and Z is
-// converted to FP64 with integer operations only (leading-zero count,
-// shift, round to nearest with ties away from zero, exponent E_m + G_n -
-// 2100 + 1023 placed directly): no FP64 instruction at all. The result is
-// FP64-accurate relative to the group's largest entry (rounding of the
-// operands at 2^-57 of their alignment, ~2^-53 from the dropped orders and
-// order 7's rounding, one final rounding).
+// Recombination without FP64 arithmetic: each accumulator of orders 0..5
+// becomes its integer by one FP32 add of 1.5 * 2^23 (the float's low
+// mantissa bits then hold P_t); orders 6 and 7 are rounded to units of 2^8
+// and 2^16 the same way. The integers are combined into one 64-bit integer
+// Z = sum_t P_t 2^(8 (5 - t)) (|Z| < 2^60) with wide integer multiply-adds,
+// and Z is converted to FP64 with integer operations only (leading-zero
+// count, shift, round to nearest with ties away from zero, exponent placed
+// directly): Y = Z * 2^(E_m + G_n - 2096), no FP64 instruction at all. The
+// result is FP64-accurate relative to the group's largest entry (rounding of
+// the operands at 2^-55 of their alignment, ~2^-53 from the dropped orders
+// and the rounding of orders 6 and 7, one final rounding).
 //
 // Work unit, group walk and Hermitian bookkeeping follow the split
 // tensor-core kernel (tq_apply_tc.cu): half of a 16 x 16 tile of canonical
@@ -76,12 +79,12 @@ __device__ unsigned int g_oz_timeouts;
 
 constexpr int kThreads = 256;  // two threads per group of a 128-group unit
 constexpr int kTile = 16;
-constexpr int kDigits = 8;                          // 7-bit digits per operand value
+constexpr int kDigits = 7;                          // balanced 8-bit digits per operand value
 constexpr int kAccs = 8;                            // one accumulator per order 0..7
-constexpr uint32_t kADigitBytes = 128 * kRowBytes;  // 128 groups x 32 BF16
+constexpr uint32_t kADigitBytes = 128 * kRowBytes;  // 128 groups x 32 FP16
 constexpr uint32_t kOffA = 0;
 constexpr uint32_t kOffB = kOffA + kDigits * kADigitBytes;
-constexpr uint32_t kOffG = kOffB + kDigits * kBTermBytes;  // 32 row exponents
+constexpr uint32_t kOffG = kOffB + (kDigits + 1) * kBTermBytes;  // (+ the zero slab B_7) 32 row exponents
 constexpr uint32_t kOffE = kOffG + 32 * 4;                // 2 x 128 half maxima
 constexpr uint32_t kOffBar = kOffE + 256 * 4;
 constexpr uint32_t kOffTmem = kOffBar + 8;
@@ -90,56 +93,54 @@ constexpr uint32_t kSmemBytes = kOffFlag + 4;
 constexpr uint32_t kTmemCols = 256;
 constexpr int kCtasPerSm = 2;
 
-// Digit I of the magnitude held in f's bits 16..22 (already shifted there),
-// as the FP32 number d_I 2^(-7 I): d_I is placed in mantissa bits 16..22 of
-// a float of exponent 2^(7 - 7 I) and that float's leading 1 is subtracted
-// off (exact; the sign is applied to the packed BF16 pair afterwards).
-template <int I>
-__device__ __forceinline__ float digit(uint32_t f) {
-  constexpr uint32_t bias = (uint32_t)(134 - 7 * I) << 23;
-  return __uint_as_float((f & 0x7f0000u) | bias) - __uint_as_float(bias);
-}
-
-// The eight digit magnitudes of v aligned to biased exponent E (v's exponent
-// <= E): the significand shifted right by E - e_v and rounded to nearest
-// (ties away from zero), F < 2^56, digit i = bits 49 - 7 i .. 55 - 7 i of F.
-// Zeros and subnormals (exponent field 0) give zero digits. *sgn: v's sign
-// bit (bit 31).
-__device__ __forceinline__ void digits8(double v, int E, float d[kDigits], uint32_t* sgn) {
-  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-  *sgn = hi & 0x80000000u;
+// F + 0x0080808080808080 for v's significand aligned to biased exponent E
+// (v's exponent <= E): shifted right by E - e_v and rounded to nearest
+// (ties away from zero), F < 2^54. Byte 6 - i of the result, minus 128, is
+// digit i. Zeros and subnormals (exponent field 0) give F = 0 (every byte
+// 0x80).
+__device__ __forceinline__ unsigned long long aligned_offset(uint32_t hi, uint32_t lo, int E) {
   const int ev = (int)((hi >> 20) & 0x7ffu);
   const int sh = E - ev;
-  const unsigned long long M3 = (((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) << 3;
+  const unsigned long long M1 = (((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) << 1;
   const unsigned long long F =
-      (ev == 0 || sh > 56) ? 0ull : sh == 0 ? M3 : (((M3 >> (sh - 1)) + 1ull) >> 1);
-  const uint32_t fh = (uint32_t)(F >> 32), fl = (uint32_t)F;  // bits 32..55 and 0..31
-  d[0] = digit<0>(fh >> 1);                         // bits 49..55
-  d[1] = digit<1>(fh << 6);                         // 42..48
-  d[2] = digit<2>(fh << 13);                        // 35..41
-  d[3] = digit<3>(__funnelshift_r(fl, fh, 12));     // 28..34
-  d[4] = digit<4>(fl >> 5);                         // 21..27
-  d[5] = digit<5>(fl << 2);                         // 14..20
-  d[6] = digit<6>(fl << 9);                         // 7..13
-  d[7] = digit<7>(fl << 16);                        // 0..6
+      (ev == 0 || sh > 54) ? 0ull : sh == 0 ? M1 : (((M1 >> (sh - 1)) + 1ull) >> 1);
+  return F + 0x0080808080808080ull;
 }
 
 __device__ __forceinline__ uint32_t abs_hi(double v) { return (uint32_t)__double2hiint(v) & 0x7fffffffu; }
 
+// FP16x2 word of digit I of a complex entry (low half: Re, high half: Im):
+// the two digit bytes are placed in the low mantissa bytes of FP16 1024
+// (0x6400), so each half reads 1024 + byte; subtracting 1152 = 1024 + 128
+// leaves byte - 128 exactly; the entry's signs are applied last.
+template <int I>
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long fr, unsigned long long fi, uint32_t sign) {
+  constexpr int k = 6 - I;  // byte of F + offset
+  const uint32_t r = k >= 4 ? (uint32_t)(fr >> 32) : (uint32_t)fr;
+  const uint32_t i = k >= 4 ? (uint32_t)(fi >> 32) : (uint32_t)fi;
+  const uint32_t w = (__byte_perm(r, i, (uint32_t)((k % 4) | ((4 + k % 4) << 8))) & 0x00ff00ffu) | 0x64006400u;
+  uint32_t d;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(w), "r"(0x64806480u));
+  return d ^ sign;
+}
+
 // Stores the digit words of 4 consecutive complex entries (one 16-byte chunk
-// of every digit operand's row): BF16 pairs (Re digit, Im digit) with the
-// entries' signs.
+// of every digit operand's row).
 __device__ __forceinline__ void store_chunk(const double2 x[4], int E, uint32_t row_chunk, uint32_t digit_bytes) {
   uint32_t w[kDigits][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    float dr[kDigits], di[kDigits];
-    uint32_t sr, si;
-    digits8(x[e].x, E, dr, &sr);
-    digits8(x[e].y, E, di, &si);
-    const uint32_t sign = (sr >> 16) | si;  // sign bits of the low and high BF16 halves
-#pragma unroll
-    for (int i = 0; i < kDigits; ++i) w[i][e] = pack_bf16x2(dr[i], di[i]) ^ sign;
+    const uint32_t rh = (uint32_t)__double2hiint(x[e].x), rl = (uint32_t)__double2loint(x[e].x);
+    const uint32_t ih = (uint32_t)__double2hiint(x[e].y), il = (uint32_t)__double2loint(x[e].y);
+    const unsigned long long fr = aligned_offset(rh, rl, E), fi = aligned_offset(ih, il, E);
+    const uint32_t sign = ((rh & 0x80000000u) >> 16) | (ih & 0x80000000u);  // FP16 sign bits of both halves
+    w[0][e] = digit_pair<0>(fr, fi, sign);
+    w[1][e] = digit_pair<1>(fr, fi, sign);
+    w[2][e] = digit_pair<2>(fr, fi, sign);
+    w[3][e] = digit_pair<3>(fr, fi, sign);
+    w[4][e] = digit_pair<4>(fr, fi, sign);
+    w[5][e] = digit_pair<5>(fr, fi, sign);
+    w[6][e] = digit_pair<6>(fr, fi, sign);
   }
 #pragma unroll
   for (int i = 0; i < kDigits; ++i) sts128(row_chunk + i * digit_bytes, w[i][0], w[i][1], w[i][2], w[i][3]);
@@ -175,6 +176,8 @@ __device__ __forceinline__ void build_b_digits(unsigned char* smem, uint32_t sba
   const int G = (int)(mx >> 20);
   if (quarter == 0) reinterpret_cast<int*>(smem + kOffG)[n] = G;
   store_chunk(r, G, sbase + kOffB + core_off(n, quarter), kBTermBytes);
+  // the zero slab B_7: digit 0's MMA reaches it and clears accumulator block 7
+  sts128(sbase + kOffB + kDigits * kBTermBytes + core_off(n, quarter), 0u, 0u, 0u, 0u);
 }
 
 // 64-bit integer multiply-add of a 32-bit word: c + a * b (unsigned, mod 2^64).
@@ -186,37 +189,37 @@ __device__ __forceinline__ unsigned long long mad_wide(uint32_t a, uint32_t b, u
 
 // FP32 bit pattern of 1.5 * 2^(23 - u): adding it to a multiple of 2^-u below
 // 2^(22 - u) in magnitude leaves that multiple, in units of 2^-u, plus 2^22 in
-// the low mantissa bits (exact).
+// the low mantissa bits (exact); for u < 0 the sum is rounded to units of
+// 2^-u.
 __host__ __device__ constexpr uint32_t magic_bits(int u) { return ((uint32_t)(150 - u) << 23) | 0x400000u; }
 
 // sum over the accumulators of the magic patterns at their weights (mod
-// 2^64), subtracted once from the combined raw patterns (orders 6 and 7 both
-// in units of 2^-42)
+// 2^64), subtracted once from the combined raw patterns
 __host__ __device__ constexpr unsigned long long magic_offset() {
-  return ((unsigned long long)magic_bits(0) << 42) + ((unsigned long long)magic_bits(7) << 35) +
-         ((unsigned long long)magic_bits(14) << 28) + ((unsigned long long)magic_bits(21) << 21) +
-         ((unsigned long long)magic_bits(28) << 14) + ((unsigned long long)magic_bits(35) << 7) +
-         2ull * (unsigned long long)magic_bits(42);
+  return ((unsigned long long)magic_bits(0) << 40) + ((unsigned long long)magic_bits(0) << 32) +
+         ((unsigned long long)magic_bits(0) << 24) + ((unsigned long long)magic_bits(0) << 16) +
+         ((unsigned long long)magic_bits(0) << 8) + (unsigned long long)magic_bits(0) +
+         (unsigned long long)magic_bits(-8) + (unsigned long long)magic_bits(-16);
 }
 
-// Real output from its 8 accumulator values (orders 0..7): Z, their sum in
-// integer units of 2^-42 of order 0, as the FP64 number Z * 2^scale (scale =
-// E + G - 2100), built from Z's bits with integer operations.
+// Real output from its 8 accumulator values (orders 0..7): Z = sum_t P_t
+// 2^(8 (5 - t)) (orders 6 and 7 rounded) as the FP64 number Z * 2^scale
+// (scale = E + G - 2096), built from Z's bits with integer operations.
 __device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
-  const uint32_t b0 = __float_as_uint(c[0] + __uint_as_float(magic_bits(0)));
-  const uint32_t b1 = __float_as_uint(c[1] + __uint_as_float(magic_bits(7)));
-  const uint32_t b2 = __float_as_uint(c[2] + __uint_as_float(magic_bits(14)));
-  const uint32_t b3 = __float_as_uint(c[3] + __uint_as_float(magic_bits(21)));
-  const uint32_t b4 = __float_as_uint(c[4] + __uint_as_float(magic_bits(28)));
-  const uint32_t b5 = __float_as_uint(c[5] + __uint_as_float(magic_bits(35)));
-  const uint32_t b6 = __float_as_uint(c[6] + __uint_as_float(magic_bits(42)));
-  const uint32_t b7 = __float_as_uint(c[7] + __uint_as_float(magic_bits(42)));  // rounded to 2^-42
-  unsigned long long Z = (unsigned long long)(b0 * 128u + b1) << 35;  // wraps mod 2^64 like the rest
-  Z = mad_wide(b2, 1u << 28, Z);
-  Z = mad_wide(b3, 1u << 21, Z);
-  Z = mad_wide(b4, 1u << 14, Z);
-  Z = mad_wide(b5, 1u << 7, Z);
-  Z += (unsigned long long)b6 + b7;
+  const float m0 = __uint_as_float(magic_bits(0));
+  const uint32_t b0 = __float_as_uint(c[0] + m0);
+  const uint32_t b1 = __float_as_uint(c[1] + m0);
+  const uint32_t b2 = __float_as_uint(c[2] + m0);
+  const uint32_t b3 = __float_as_uint(c[3] + m0);
+  const uint32_t b4 = __float_as_uint(c[4] + m0);
+  const uint32_t b5 = __float_as_uint(c[5] + m0);
+  const uint32_t b6 = __float_as_uint(c[6] + __uint_as_float(magic_bits(-8)));   // rounded to units of 2^8
+  const uint32_t b7 = __float_as_uint(c[7] + __uint_as_float(magic_bits(-16)));  // rounded to units of 2^16
+  unsigned long long Z = (unsigned long long)(b0 * 256u + b1) << 32;  // wraps mod 2^64 like the rest
+  Z = mad_wide(b2, 1u << 24, Z);
+  Z = mad_wide(b3, 1u << 16, Z);
+  Z = mad_wide(b4, 1u << 8, Z);
+  Z += (unsigned long long)b5 + b6 + b7;
   Z -= magic_offset();
   // |Z| normalised to bit 63, rounded to 53 bits (a carry into bit 53 lands
   // in the exponent field), placed under the biased exponent 1086 - lz +
@@ -369,15 +372,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
     if (*s_abort) break;
     if (tid == 0 && !skip_mma) {
       fence_after_sync();
-      // A digit i against the stacked B_0 .. B_(7-i) (N = 32 (8 - i)) adds
-      // its products of orders i .. 7 to accumulator blocks i .. 7; the
-      // first MMA (digit 0, N = 256) overwrites every block
+      // A digit i against the stacked B_0 .. B_(7-i) (N = 32 (8 - i); B_7 is
+      // the zero slab) adds its products of orders i .. 7 to accumulator
+      // blocks i .. 7; the first MMA (digit 0, N = 256) overwrites every block
 #pragma unroll
       for (int ia = 0; ia < kDigits; ++ia)
 #pragma unroll
         for (int kh = 0; kh < 2; ++kh)
           mma_bf16_n(tmem + (uint32_t)(32 * ia), a_desc0 + (uint64_t)((ia * kADigitBytes + kh * 256) >> 4),
-                     b_desc0 + (uint64_t)((kh * 256) >> 4), idesc_m128(32 * (kDigits - ia)),
+                     b_desc0 + (uint64_t)((kh * 256) >> 4), idesc_m128_f16(32 * (8 - ia)),
                      (ia == 0 && kh == 0) ? 0u : 1u);
       commit(bar);
     }
@@ -406,8 +409,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
           ci[a] = __uint_as_float(cv[a][2 * e + 1]);
         }
         double2 y;
-        y.x = recombine(cr, E + s_G[2 * o] - 2100);
-        y.y = recombine(ci, E + s_G[2 * o + 1] - 2100);
+        y.x = recombine(cr, E + s_G[2 * o] - 2096);
+        y.y = recombine(ci, E + s_G[2 * o + 1] - 2096);
         bool up;
         const unsigned int idx = entry_index(g.rb, g.cb, 4 * ch + e, b0, b1, N, &up);
         if (up) {

@@ -122,7 +122,7 @@ def test_batch_job_alone_equals_in_mix_and_single_state(tq):
         alone.wait()
         assert np.array_equal(alone.rho(0), mix.rho(j))          # bitwise: same kernels, same order
         assert np.array_equal(alone.result(0), mix.result(j))
-        with tq.State(n, "fp64") as st:    # both compute the canonical groups, same arithmetic
+        with tq.State(n, "fp64", engine="dfma") as st:    # both compute the canonical groups, same DFMA arithmetic
             st.run(ops, width=2)
             assert np.array_equal(st.rho(), mix.rho(j))
         alone.free()

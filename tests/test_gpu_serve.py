@@ -24,7 +24,8 @@ def _requests(count, seed, n_lo=2, n_hi=9):
 
 
 def _single(tq, precision, n, ops, masks):
-    with tq.State(n, precision, hermitian=precision == "fp64") as st:   # FP64: the same canonical-group arithmetic
+    # FP64: the same canonical-group DFMA arithmetic as the batch kernel
+    with tq.State(n, precision, hermitian=precision == "fp64", engine="dfma") as st:
         st.run(ops, width=2)
         tr = st.trace()
         return np.concatenate([[tr.real, tr.imag], st.expect_z(masks)])

@@ -1,19 +1,22 @@
 """CPU pins of the arithmetic of the FP64-accurate tensor-core pass
-(csrc/tq_apply_oz.cu), emulated bit by bit in numpy: every FP64 operand cut
-into eight 7-bit digits of a 56-bit fixed-point number aligned to the largest
-exponent of its group (inputs) or row (superoperator), the digit products
+(csrc/tq_apply_oz.cu), emulated bit by bit in numpy: every FP64 operand's
+significand aligned to the largest exponent of its group (inputs) or row
+(superoperator), rounded to nearest (54 bits), cut into seven balanced 8-bit
+digits (the bytes of F + 0x0080808080808080, minus 128), the digit products
 summed exactly per order t = i + j (orders 0..7, each in its own FP32
-accumulator), each accumulator turned into its integer by the
-1.5 * 2^(23 - u) float addition (order 7 rounded to units of 2^-42), the
+accumulator), each accumulator turned into its integer by the 1.5 * 2^23
+float addition (orders 6 and 7 rounded to units of 2^8 and 2^16), the
 integers combined in wrapped 64-bit arithmetic and converted to FP64 with
-integer operations only, the exponent placed directly. The exact reference is the dot product in rational arithmetic. These
-pin the digit layout, the orders, the magic constants and the scaling; the GPU
-tests hold the kernel itself to the oracle."""
+integer operations only, the exponent placed directly. The exact reference is
+the dot product in rational arithmetic. These pin the digit layout, the
+orders, the magic constants and the scaling; the GPU tests hold the kernel
+itself to the oracle."""
 from fractions import Fraction
 
 import numpy as np
 
 MASK64 = (1 << 64) - 1
+OFFSET = 0x0080808080808080
 
 
 def fields(v: float):
@@ -21,24 +24,38 @@ def fields(v: float):
     return b >> 63, (b >> 52) & 0x7FF, b & ((1 << 52) - 1)
 
 
-def digits8(v: float, E: int):
-    """The kernel's digits: +-d_i 2^(-7 i) as float32, d_i = 7-bit digit i of
-    F, the significand aligned to biased exponent E and rounded to nearest."""
-    sgn, ev, frac = fields(v)
+def aligned_offset(v: float, E: int) -> int:
+    """F + 0x0080808080808080: v's significand aligned to biased exponent E
+    and rounded to nearest (ties away from zero), F < 2^54."""
+    _, ev, frac = fields(v)
     sh = E - ev
-    M3 = ((1 << 52) | frac) << 3
-    if ev == 0 or sh > 56:
+    M1 = ((1 << 52) | frac) << 1
+    if ev == 0 or sh > 54:
         F = 0
     elif sh == 0:
-        F = M3
+        F = M1
     else:
-        F = ((M3 >> (sh - 1)) + 1) >> 1
-    assert F < (1 << 56)
-    out = []
-    for i in range(8):
-        d = (F >> (49 - 7 * i)) & 0x7F
-        out.append(np.float32((-1.0 if sgn else 1.0) * d * 2.0 ** (-7 * i)))
-    return out
+        F = ((M1 >> (sh - 1)) + 1) >> 1
+    assert F < (1 << 54)
+    return F + OFFSET
+
+
+def fp16_digit(byte: int) -> float:
+    """The kernel's FP16 arithmetic on one half: the byte placed in the low
+    mantissa byte of FP16 1024, minus 1152 (both steps exact in FP16)."""
+    w = np.array([0x6400 | byte], dtype=np.uint16).view(np.float16)[0]
+    d = np.float16(w - np.float16(1152.0))
+    assert float(d) == byte - 128
+    return float(d)
+
+
+def digits7(v: float, E: int):
+    """The seven digits of v (sign applied): integers in [-128, 128)."""
+    sgn = fields(v)[0]
+    Fp = aligned_offset(v, E)
+    assert Fp >> 56 == 0                                   # the offset never carries out of byte 6
+    d = [fp16_digit((Fp >> (8 * (6 - i))) & 0xFF) for i in range(7)]
+    return [-x if sgn else x for x in d]
 
 
 def max_exp(vals):
@@ -76,32 +93,30 @@ def int_to_f64_scaled(Z, scale):
 
 def recombine(c, scale):
     """c: 8 float32 accumulator values, orders 0..7."""
-    b = [magic_int(a, u) for a, u in zip(c[:7], (0, 7, 14, 21, 28, 35, 42))]
-    b.append(magic_int(c[7], 42))                        # order 7 rounded to units of 2^-42
-    Z = (((b[0] * 128 + b[1]) & 0xFFFFFFFF) << 35) & MASK64
-    Z = (Z + b[2] * (1 << 28)) & MASK64
-    Z = (Z + b[3] * (1 << 21)) & MASK64
-    Z = (Z + b[4] * (1 << 14)) & MASK64
-    Z = (Z + b[5] * (1 << 7)) & MASK64
-    Z = (Z + b[6] + b[7]) & MASK64
-    K = ((magic_bits(0) << 42) + (magic_bits(7) << 35) + (magic_bits(14) << 28) + (magic_bits(21) << 21)
-         + (magic_bits(28) << 14) + (magic_bits(35) << 7) + 2 * magic_bits(42)) & MASK64
+    b = [magic_int(a, 0) for a in c[:6]] + [magic_int(c[6], -8), magic_int(c[7], -16)]
+    Z = (((b[0] * 256 + b[1]) & 0xFFFFFFFF) << 32) & MASK64
+    Z = (Z + b[2] * (1 << 24)) & MASK64
+    Z = (Z + b[3] * (1 << 16)) & MASK64
+    Z = (Z + b[4] * (1 << 8)) & MASK64
+    Z = (Z + b[5] + b[6] + b[7]) & MASK64
+    K = (sum(magic_bits(0) << (8 * s) for s in range(6)) + magic_bits(-8) + magic_bits(-16)) & MASK64
     return int_to_f64_scaled((Z - K) & MASK64, scale)
 
 
 def oz_dot(x, R_row):
     """One real output: sum_k R_row[k] x[k] the kernel's way."""
     E, G = max_exp(x), max_exp(R_row)
-    A = np.array([digits8(float(v), E) for v in x])      # [k][i]
-    B = np.array([digits8(float(v), G) for v in R_row])  # [k][j]
+    A = np.array([digits7(float(v), E) for v in x])      # [k][i]
+    B = np.array([digits7(float(v), G) for v in R_row])  # [k][j]
     c = []
-    for t in range(8):                                   # every order exact (summed in float64, exact here)
+    for t in range(8):                                   # orders 0..7, each exact
         acc = 0.0
-        for i in range(t + 1):
-            acc += float(np.dot(A[:, i].astype(np.float64), B[:, t - i].astype(np.float64)))
-        assert float(np.float32(acc)) == acc             # representable: FP32 accumulation is exact
+        for i in range(7):
+            if 0 <= t - i < 7:
+                acc += float(np.dot(A[:, i], B[:, t - i]))
+        assert abs(acc) < 2 ** 22 and float(np.float32(acc)) == acc   # FP32 accumulation is exact
         c.append(np.float32(acc))
-    return recombine(c, E + G - 2100), E, G
+    return recombine(c, E + G - 2096), E, G
 
 
 def exact_dot(x, r):
@@ -117,22 +132,23 @@ def test_digits_reassemble_the_rounded_value():
     for _ in range(2000):
         v = float(rng.standard_normal() * 10.0 ** rng.uniform(-12, 2))
         E = fields(v)[1] + int(rng.integers(0, 20))
-        d = digits8(v, E)
-        back = sum(Fraction(float(t)) for t in d) * Fraction(2) ** (E - 1078 + 49)
-        assert abs(back - Fraction(v)) <= Fraction(2) ** (E - 1078 - 1)   # half a unit of 2^(E-1078)
-        for i, t in enumerate(d):
-            q = abs(float(t)) * 2.0 ** (7 * i)
-            assert q == int(q) and q < 128                                 # a 7-bit digit, exact in BF16
+        d = digits7(v, E)
+        back = sum(Fraction(int(t)) * 256 ** (6 - i) for i, t in enumerate(d)) * Fraction(2) ** (E - 1076)
+        assert abs(back - Fraction(v)) <= Fraction(2) ** (E - 1076 - 1)   # half a unit of 2^(E-1076)
+        assert all(abs(t) <= 128 and t == int(t) for t in d)              # integers, exact in FP16 (sign applied)
+        assert abs(d[0]) <= 64                                           # F < 2^54: the top digit stays small
 
 
 def test_exact_orders_stay_below_the_magic_range():
-    # worst case: every digit 127 (all values at the top of the alignment)
-    x = np.full(32, np.nextafter(2.0, 0.0))
-    d = digits8(float(x[0]), fields(float(x[0]))[1])
-    # a 53-bit significand shifted by 3: the last digit keeps 4 bits
-    assert [round(abs(float(t)) * 2.0 ** (7 * i)) for i, t in enumerate(d)] == [127] * 7 + [120]
+    # the largest digit magnitudes: every order's integer stays below 2^22,
+    # where the 1.5 * 2^23 addition extracts it exactly
     for t in range(8):
-        assert (t + 1) * 32 * 127 * 127 < 2 ** 22
+        pairs = min(t + 1, 7, 14 - t)
+        assert pairs * 32 * 128 * 128 < 2 ** 22
+    x = np.full(32, np.nextafter(2.0, 0.0))
+    r = -x
+    y, _, _ = oz_dot(x, r)
+    assert abs(Fraction(y) - exact_dot(x, r)) <= abs(exact_dot(x, r)) * Fraction(1, 2 ** 52)
 
 
 def test_recombined_dot_products_are_fp64_accurate():
@@ -148,8 +164,9 @@ def test_recombined_dot_products_are_fp64_accurate():
         y, E, G = oz_dot(x, r)
         err = abs(Fraction(y) - exact_dot(x, r))
         worst = max(worst, float(err) / (align(E) * align(G)))
-    # 32 operand pairs, each rounded at 2^-57 of its alignment, dropped orders
-    # and one final rounding: below 2^-51 of the product of the alignments
+    # 32 operand pairs, each rounded at 2^-55 of its alignment, dropped orders,
+    # the rounding of orders 6 and 7 and one final rounding: below 2^-51 of
+    # the product of the alignments (measured: ~2 x 2^-53)
     assert worst < 2.0 ** -51, worst / 2.0 ** -53
 
 
@@ -180,8 +197,7 @@ def test_integer_conversion_rounds_to_nearest():
         s = int(rng.integers(-60, 60))
         got = int_to_f64_scaled(z & MASK64, s)
         want = Fraction(z) * Fraction(2) ** s
-        # within half a unit in the last place of the result
-        assert abs(Fraction(got) - want) <= abs(want) * Fraction(1, 2 ** 53)
+        assert abs(Fraction(got) - want) <= abs(want) * Fraction(1, 2 ** 53)   # half an ulp of the result
     assert int_to_f64_scaled(0, 5) == 0.0
     assert int_to_f64_scaled((1 << 53) + 1, 0) == float((1 << 53) + 2)   # a tie rounds away from zero
     assert int_to_f64_scaled((-(1 << 53) - 1) & MASK64, 0) == -float((1 << 53) + 2)
