@@ -434,7 +434,10 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
     return cuda_fail(s, e);
   }
   SparseBlock* sps = static_cast<SparseBlock*>(P.sps.ptr);
-  if (e == cudaSuccess && P.n_sparse > 0)
+  // row lists serve the DFMA kernels only: none are needed when every block
+  // of width <= 2 runs on the tensor-core FP64 engine
+  const bool rows_unused = s->prec == TQ_FP64 && s->herm_mode && s->herm_ok && fp64_on_tensor(s) && oz_eligible(s->n, 2);
+  if (e == cudaSuccess && P.n_sparse > 0 && !rows_unused)
     e = timed(s, K_PACK, 1, [&] {
       return launch_compress_sparse(sb64, d_blk, reinterpret_cast<const SparseWork*>(d + P.o_spw), P.n_sparse, sps,
                                     s->stream);
@@ -442,7 +445,7 @@ tq_status enqueue_program(tq_state* s, const tq_program& P) {
   // profiling: copy every row list's rowptr back, so that the flops of a
   // row-list launch count the nonzeros it actually applied
   const int* counts = nullptr;
-  if (e == cudaSuccess && s->prof_on && P.n_sparse > 0) {
+  if (e == cudaSuccess && s->prof_on && P.n_sparse > 0 && !rows_unused) {
     constexpr size_t kRow = sizeof(SparseBlock::rowptr);
     int* h = s->counts.take((size_t)P.n_sparse * (kRow / sizeof(int)));
     if (!h) return TQ_ERR_OOM;

@@ -362,7 +362,7 @@ def test_profile_counts_the_row_list_nonzeros_applied(tq):
              ([("ad", [5], (0.2,))], "apply_f64_sparse_w1", 1, 5),
              ([("cx", [1, 4], ())], "apply_f64_sparse_w2", 2, 16)]
     for ops, kind, w, nnz in cases:
-        with tq.State(n, "fp64") as st:
+        with tq.State(n, "fp64", engine="dfma") as st:
             st.profile(True)
             st.run(ops, width=0)
             stats = st.profile_stats()
