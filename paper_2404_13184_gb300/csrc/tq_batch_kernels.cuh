@@ -83,6 +83,123 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+// Split width-2 products of tile items in the Pauli basis. Every block is a Kraus map, so
+// its superoperator S preserves Hermiticity, and in the basis of Pauli
+// products (T: per qubit, the entries (r, c) = 00, 10, 01, 11 of its 2 x 2
+// block become I = a00 + a11, X = a01 + a10, Y = i (a01 - a10), Z = a00 -
+// a11) it is a REAL 16 x 16 matrix R = T S T^dagger / 4. A group's 16
+// entries (not Hermitian themselves) are mapped by y = T^dagger R' T x with
+// R' = R / 4: real times complex, 512 FMA instead of the 1,024 of S x,
+// plus 128 adds for the two basis changes (butterflies, coefficients +-1,
+// +-i). Slots: the Pauli pair (P0, P1) sits where local entry
+// {0, 1, 4, 5}[P0] + {0, 2, 8, 10}[P1] sat.
+__device__ __forceinline__ void pauli_fwd(float2 x[16]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      // qubit 0: entries b, b + 1 (r0), b + 4 (c0), b + 5 at b in {0, 2, 8, 10};
+      // qubit 1: b, b + 2 (r1), b + 8 (c1), b + 10 at b in {0, 1, 4, 5}
+      const int b = q == 0 ? (t & 1) * 2 + (t >> 1) * 8 : (t & 1) + (t >> 1) * 4;
+      const int s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
+      const float2 a00 = x[b], a10 = x[b + s10], a01 = x[b + s01], a11 = x[b + s10 + s01];
+      x[b] = make_float2(a00.x + a11.x, a00.y + a11.y);                     // I
+      x[b + s10] = make_float2(a01.x + a10.x, a01.y + a10.y);               // X
+      x[b + s01] = make_float2(a10.y - a01.y, a01.x - a10.x);               // Y = i (a01 - a10)
+      x[b + s10 + s01] = make_float2(a00.x - a11.x, a00.y - a11.y);         // Z
+    }
+  }
+}
+__device__ __forceinline__ void pauli_inv(float2 x[16]) {
+#pragma unroll
+  for (int q = 1; q >= 0; --q) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int b = q == 0 ? (t & 1) * 2 + (t >> 1) * 8 : (t & 1) + (t >> 1) * 4;
+      const int s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
+      const float2 I = x[b], X = x[b + s10], Y = x[b + s01], Z = x[b + s10 + s01];
+      x[b] = make_float2(I.x + Z.x, I.y + Z.y);                             // a00 = I + Z
+      x[b + s10] = make_float2(X.x - Y.y, X.y + Y.x);                       // a10 = X + i Y
+      x[b + s01] = make_float2(X.x + Y.y, X.y - Y.x);                       // a01 = X - i Y
+      x[b + s10 + s01] = make_float2(I.x - Z.x, I.y - Z.y);                 // a11 = I - Z
+    }
+  }
+}
+// y = T^dagger R' T x in place (R' row-major in shared memory, read as
+// float4); the 16 products wait in this thread's shared-memory column
+// col[a * kThreads] while x is still in use, which keeps the registers of
+// both out of the same instant.
+__device__ __forceinline__ void pauli_apply(float2 x[16], const float* __restrict__ R, float2* col) {
+  pauli_fwd(x);
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b4 = 0; b4 < 4; ++b4) {
+      const float4 r = reinterpret_cast<const float4*>(R + a * 16)[b4];
+      acc.x = fmaf(r.x, x[4 * b4].x, acc.x);
+      acc.y = fmaf(r.x, x[4 * b4].y, acc.y);
+      acc.x = fmaf(r.y, x[4 * b4 + 1].x, acc.x);
+      acc.y = fmaf(r.y, x[4 * b4 + 1].y, acc.y);
+      acc.x = fmaf(r.z, x[4 * b4 + 2].x, acc.x);
+      acc.y = fmaf(r.z, x[4 * b4 + 2].y, acc.y);
+      acc.x = fmaf(r.w, x[4 * b4 + 3].x, acc.x);
+      acc.y = fmaf(r.w, x[4 * b4 + 3].y, acc.y);
+    }
+    col[a * kThreads] = acc;
+  }
+#pragma unroll
+  for (int a = 0; a < 16; ++a) x[a] = col[a * kThreads];
+  pauli_inv(x);
+}
+// R' = T S T^dagger / 16 of a width-2 superoperator S (16 x 16 complex, shared
+// memory), one entry per thread (256 threads): row sa of T has 4 nonzeros,
+// the products of the two qubits' Pauli coefficients.
+__device__ __forceinline__ void pauli_row(int slot, int l[4], float2 coef[4]) {
+  const int P[2] = {((slot & 1) ? 1 : 0) | ((slot & 4) ? 2 : 0), ((slot & 2) ? 1 : 0) | ((slot & 8) ? 2 : 0)};
+  int rc[2][2][2];     // per qubit: two (r, c) pairs
+  float2 cf[2][2];     // and their coefficients
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    switch (P[j]) {
+      case 0: rc[j][0][0] = 0; rc[j][0][1] = 0; rc[j][1][0] = 1; rc[j][1][1] = 1;
+              cf[j][0] = make_float2(1.f, 0.f); cf[j][1] = make_float2(1.f, 0.f); break;   // I: 00, 11
+      case 1: rc[j][0][0] = 0; rc[j][0][1] = 1; rc[j][1][0] = 1; rc[j][1][1] = 0;
+              cf[j][0] = make_float2(1.f, 0.f); cf[j][1] = make_float2(1.f, 0.f); break;   // X: 01, 10
+      case 2: rc[j][0][0] = 0; rc[j][0][1] = 1; rc[j][1][0] = 1; rc[j][1][1] = 0;
+              cf[j][0] = make_float2(0.f, 1.f); cf[j][1] = make_float2(0.f, -1.f); break;  // Y: i 01, -i 10
+      default: rc[j][0][0] = 0; rc[j][0][1] = 0; rc[j][1][0] = 1; rc[j][1][1] = 1;
+              cf[j][0] = make_float2(1.f, 0.f); cf[j][1] = make_float2(-1.f, 0.f); break;  // Z: 00, -11
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int r0 = rc[0][u][0], c0 = rc[0][u][1], r1 = rc[1][v][0], c1 = rc[1][v][1];
+      l[2 * u + v] = r0 + 2 * r1 + 4 * c0 + 8 * c1;
+      coef[2 * u + v] = make_float2(cf[0][u].x * cf[1][v].x - cf[0][u].y * cf[1][v].y,
+                                    cf[0][u].x * cf[1][v].y + cf[0][u].y * cf[1][v].x);
+    }
+}
+__device__ __forceinline__ void pauli_transform(const float2* sS, float* R) {
+  const int sa = threadIdx.x / 16, sb = threadIdx.x % 16;
+  int la[4], lb[4];
+  float2 ca[4], cb[4];
+  pauli_row(sa, la, ca);
+  pauli_row(sb, lb, cb);
+  float acc = 0.f;  // Re sum_{u,v} ca[u] S[la[u]][lb[v]] conj(cb[v])
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float2 sv = sS[la[u] * 16 + lb[v]];
+      const float2 t = make_float2(ca[u].x * sv.x - ca[u].y * sv.y, ca[u].x * sv.y + ca[u].y * sv.x);
+      acc += t.x * cb[v].x + t.y * cb[v].y;  // Re (t conj(cb))
+    }
+  R[sa * 16 + sb] = acc * (1.f / 16.f);
+}
+
 // One canonical group of a width-K split block on the shared-memory copy of
 // rho (resident items): gather its 4^K entries, multiply by S (shared
 // memory), scatter back. t indexes the canonical groups (row rest <= column
@@ -266,7 +383,7 @@ __device__ __forceinline__ void apply_group_lists_resident(double2* sR, unsigned
 // One canonical 16 x 16 tile u of a width-K split block (see Tile16).
 template <int K>
 __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, const ApplyParams& p,
-                                             const float2* sS, const Tile16& t) {
+                                             const float2* sS, const Tile16& t, const float* ptm, float2* col) {
   constexpr int D = 1 << (2 * K);
   // a warp covers 8 row rests x 4 column rests (full 32-byte sectors in both
   // orientations)
@@ -288,11 +405,17 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
     if (!up) v.y = -v.y;
     x[l] = v;
   }
+  if constexpr (K == 2) pauli_apply(x, ptm, col);  // y = S x in the Pauli basis
 #pragma unroll
   for (int o = 0; o < D; ++o) {
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc;
+    if constexpr (K == 2) {
+      acc = x[o];
+    } else {
+      acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int l = 0; l < D; ++l) Cx<float2>::fma(acc, sS[o * D + l], x[l]);
+      for (int l = 0; l < D; ++l) Cx<float2>::fma(acc, sS[o * D + l], x[l]);
+    }
     const unsigned r = rbase + t.rt[o], c = cbase + t.ct[o];
     if (r <= c) {
       rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
@@ -308,7 +431,8 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
 // counts as zero). The row lists take rows in order, each thread i < D
 // placing row i after the counts of rows < i.
 template <typename T2>
-__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl, Tile16* t16) {
+__device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl, Tile16* t16,
+                                            float* ptm) {
   static_assert(sizeof(BBlk) % 8 == 0 && sizeof(BBlk) / 8 <= kThreads, "descriptor copied one word per thread");
   if (threadIdx.x < sizeof(BBlk) / 8)  // in parallel: one 8-byte word per thread
     reinterpret_cast<unsigned long long*>(s_blk)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(blk)[threadIdx.x];
@@ -337,6 +461,10 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
         t16->rt[threadIdx.x] = rt;
         t16->ct[threadIdx.x] = ct;
       }
+    }
+    if (K == 2) {  // the Pauli-basis matrix R' of the block (split width 2)
+      __syncthreads();
+      pauli_transform(reinterpret_cast<const float2*>(sS), ptm);
     }
   } else {
     const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(S);
@@ -380,6 +508,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
   __shared__ BBlk s_blk;
   __shared__ RowLists s_rl;
   __shared__ Tile16 s_t16;
+  __shared__ __align__(16) float s_ptm[256];  // Pauli-basis matrix of a split width-2 block
   __shared__ int s_idx;
   constexpr bool kF64 = sizeof(T2) == 16;
   for (;;) {
@@ -397,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       const int N = 1 << (2 * n);
       for (int e = threadIdx.x; e < N; e += blockDim.x) sR[e] = Cx<T2>::ldcg(&rho[e]);
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
-        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16);
+        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16, s_ptm);
         const ApplyParams& p = s_blk.p;
         for (unsigned long long g = threadIdx.x; g < p.n_canon; g += blockDim.x) {
           if constexpr (kF64) {
@@ -422,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
     }
     // tile item: stage the block (independent of earlier blocks), then wait
     // until every tile of the previous block of this job is done
-    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16);
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16, s_ptm);
     if (threadIdx.x == 0 && it.block > 0) {
       const int need = jb.never_ready ? 0x7fffffff : s_blk.tile_prefix;
       long long spins = 0;
@@ -462,10 +591,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         const unsigned long long u0 = (unsigned long long)it.tile0 * upt;
         const unsigned long long u1 = min(total, u0 + (unsigned long long)it.ntiles * upt);
         for (unsigned long long u = u0; u < u1; ++u) {
+          // the resident buffer is free in tile items: one column per thread
+          float2* col = reinterpret_cast<float2*>(sR) + threadIdx.x;
           if (p.width == 1)
-            apply_tile16<1>(rho, u, p, sS, s_t16);
+            apply_tile16<1>(rho, u, p, sS, s_t16, s_ptm, col);
           else
-            apply_tile16<2>(rho, u, p, sS, s_t16);
+            apply_tile16<2>(rho, u, p, sS, s_t16, s_ptm, col);
         }
       }
     }
