@@ -72,7 +72,8 @@ int default_tile_log2(int n, int prec) {
 
 // Algorithmic flops and HBM bytes of one run (see tq_batch_work): one CTA
 // per job, threads over its blocks; FP64 counts the nonzeros of S by their
-// bit patterns, as the row-list staging does.
+// bit patterns, as the row-list staging does, and width-2 blocks of tile
+// jobs make the kernel's Pauli-basis choice (pauli_better on the same R').
 __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restrict__ blks, int prec,
                              unsigned long long* __restrict__ out) {
   const BJob& jb = jobs[blockIdx.x];
@@ -88,8 +89,23 @@ __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restri
       nnz = 0;
       for (int e = 0; e < D * D; ++e) nnz += ((bits[2 * e] | bits[2 * e + 1]) << 1) != 0ull;
     }
+    // flops per group: 8 per complex multiply-add of S (its nonzeros, or all
+    // of them), or in the Pauli basis 4 per real-times-complex multiply-add
+    // plus the 128 adds of the two basis changes
+    unsigned long long per = 8ull * nnz;
+    if (!jb.resident && bk.p.width == 2) {
+      double Rp[256], mx = 0.0;
+      for (int e = 0; e < 256; ++e) {
+        Rp[e] = pauli_entry(bk.S64, e / 16, e % 16);
+        mx = fmax(mx, fabs(Rp[e]));
+      }
+      const double thr = mx * kPauliZeroRel;
+      int nnzR = 0;
+      for (int e = 0; e < 256; ++e) nnzR += fabs(Rp[e]) > thr;
+      if (pauli_better(prec, (int)nnz, nnzR)) per = 4ull * nnzR + 128;
+    }
     const unsigned long long groups = jb.herm ? bk.p.n_canon : bk.p.n_groups;
-    fl += 8ull * nnz * groups;
+    fl += per * groups;
     if (!jb.resident) by += (jb.herm ? N + R : 2 * N) * esz;
   }
   if (jb.resident && threadIdx.x == 0 && jb.n_blocks > 0) by += 2 * N * esz;
@@ -222,7 +238,11 @@ tq_status finalize(tq_batch* b) {
   {
     const size_t esz = b->prec == TQ_FP64 ? sizeof(double2) : sizeof(float2);
     char* sbase = static_cast<char*>(b->prec == TQ_FP64 ? b->sb64.ptr : b->sb32.ptr);
-    for (BBlk& bb : hblks) bb.S = sbase + reinterpret_cast<size_t>(bb.S) * esz;
+    for (BBlk& bb : hblks) {
+      const size_t off = reinterpret_cast<size_t>(bb.S);
+      bb.S = sbase + off * esz;
+      bb.S64 = static_cast<const double2*>(b->sb64.ptr) + off;
+    }
   }
   e = cudaMemcpy(b->blob.ptr, h.data(), P.blob_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->djobs.ptr, hjobs.data(), hjobs.size() * sizeof(BJob), cudaMemcpyHostToDevice);

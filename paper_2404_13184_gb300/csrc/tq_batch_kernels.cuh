@@ -40,9 +40,10 @@ struct BJob {
 
 struct BBlk {
   ApplyParams p;
-  const void* S;    // fused superoperator, 4^w x 4^w row-major (double2 or float2)
-  int tiles;        // tile items of this block (tile jobs)
-  int tile_prefix;  // tiles of the job's earlier blocks: the wait target
+  const void* S;       // fused superoperator, 4^w x 4^w row-major (double2 or float2)
+  const double2* S64;  // the same in FP64 (both precisions): source of the Pauli-basis lists
+  int tiles;           // tile items of this block (tile jobs)
+  int tile_prefix;     // tiles of the job's earlier blocks: the wait target
 };
 
 struct BItem {
@@ -83,121 +84,121 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Split width-2 products of tile items in the Pauli basis. Every block is a Kraus map, so
-// its superoperator S preserves Hermiticity, and in the basis of Pauli
-// products (T: per qubit, the entries (r, c) = 00, 10, 01, 11 of its 2 x 2
-// block become I = a00 + a11, X = a01 + a10, Y = i (a01 - a10), Z = a00 -
-// a11) it is a REAL 16 x 16 matrix R = T S T^dagger / 4. A group's 16
-// entries (not Hermitian themselves) are mapped by y = T^dagger R' T x with
-// R' = R / 4: real times complex, 512 FMA instead of the 1,024 of S x,
-// plus 128 adds for the two basis changes (butterflies, coefficients +-1,
-// +-i). Slots: the Pauli pair (P0, P1) sits where local entry
-// {0, 1, 4, 5}[P0] + {0, 2, 8, 10}[P1] sat.
-__device__ __forceinline__ void pauli_fwd(float2 x[16]) {
+// Width-2 products of tile items in the Pauli basis. Every block is a
+// Kraus map, so its superoperator S preserves Hermiticity, and in the basis
+// of Pauli products (T: per qubit, the entries (r, c) = 00, 10, 01, 11 of
+// its 2 x 2 block become I = a00 + a11, X = a01 + a10, Y = i (a01 - a10),
+// Z = a00 - a11) it is a REAL 16 x 16 matrix R = T S T^dagger / 4. A
+// group's 16 entries (not Hermitian themselves) are mapped by y = T^dagger
+// R' T x with R' = R / 4: a real times complex product (2 multiply-adds per
+// nonzero instead of 4) between two basis changes (butterflies with
+// coefficients +-1, +-i, 128 adds per group). Gates of the circuits here
+// (Cliffords, rotations about Pauli axes) and Pauli channels are sparse in
+// this basis: the fused width-2 blocks of the 1024-circuit sweep have ~31
+// nonzeros of R' against ~120 complex nonzeros of S. R' is computed in FP64
+// from the FP64 superoperator; entries at most 2^-47 of its largest are
+// rounding residues of structural zeros and are dropped. Slots: the Pauli
+// pair (P0, P1) sits where local entry {0, 1, 4, 5}[P0] + {0, 2, 8, 10}[P1]
+// sat.
+constexpr double kPauliZeroRel = 7.105427357601002e-15;  // 2^-47
+
+template <typename T2>
+struct Sc;
+template <>
+struct Sc<float2> {
+  using T = float;
+  __device__ __forceinline__ static float2 mk(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct Sc<double2> {
+  using T = double;
+  __device__ __forceinline__ static double2 mk(double a, double b) { return make_double2(a, b); }
+};
+
+// Butterfly of one qubit on slots b, b + s10 (r = 1), b + s01 (c = 1),
+// b + s10 + s01: forward (computational -> Pauli) or inverse (T^dagger).
+template <typename T2>
+__device__ __forceinline__ void pauli_bfly_fwd(T2& a00, T2& a10, T2& a01, T2& a11) {
+  const T2 I = Sc<T2>::mk(a00.x + a11.x, a00.y + a11.y), X = Sc<T2>::mk(a01.x + a10.x, a01.y + a10.y);
+  const T2 Y = Sc<T2>::mk(a10.y - a01.y, a01.x - a10.x), Z = Sc<T2>::mk(a00.x - a11.x, a00.y - a11.y);
+  a00 = I;
+  a10 = X;
+  a01 = Y;
+  a11 = Z;
+}
+template <typename T2>
+__device__ __forceinline__ void pauli_bfly_inv(T2& I, T2& X, T2& Y, T2& Z) {
+  const T2 a00 = Sc<T2>::mk(I.x + Z.x, I.y + Z.y), a11 = Sc<T2>::mk(I.x - Z.x, I.y - Z.y);
+  const T2 a10 = Sc<T2>::mk(X.x - Y.y, X.y + Y.x), a01 = Sc<T2>::mk(X.x + Y.y, X.y - Y.x);  // X + i Y, X - i Y
+  I = a00;
+  X = a10;
+  Y = a01;
+  Z = a11;
+}
+// slot bases of the butterflies of qubit q (t < 4) and the slot strides
+__host__ __device__ __forceinline__ int pauli_base(int q, int t) { return q == 0 ? (t & 1) * 2 + (t >> 1) * 8 : (t & 1) + (t >> 1) * 4; }
+template <typename T2>
+__device__ __forceinline__ void pauli_fwd(T2 x[16]) {
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      // qubit 0: entries b, b + 1 (r0), b + 4 (c0), b + 5 at b in {0, 2, 8, 10};
-      // qubit 1: b, b + 2 (r1), b + 8 (c1), b + 10 at b in {0, 1, 4, 5}
-      const int b = q == 0 ? (t & 1) * 2 + (t >> 1) * 8 : (t & 1) + (t >> 1) * 4;
-      const int s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
-      const float2 a00 = x[b], a10 = x[b + s10], a01 = x[b + s01], a11 = x[b + s10 + s01];
-      x[b] = make_float2(a00.x + a11.x, a00.y + a11.y);                     // I
-      x[b + s10] = make_float2(a01.x + a10.x, a01.y + a10.y);               // X
-      x[b + s01] = make_float2(a10.y - a01.y, a01.x - a10.x);               // Y = i (a01 - a10)
-      x[b + s10 + s01] = make_float2(a00.x - a11.x, a00.y - a11.y);         // Z
+      const int b = pauli_base(q, t), s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
+      pauli_bfly_fwd(x[b], x[b + s10], x[b + s01], x[b + s10 + s01]);
     }
-  }
 }
-__device__ __forceinline__ void pauli_inv(float2 x[16]) {
+template <typename T2>
+__device__ __forceinline__ void pauli_inv(T2 x[16]) {
 #pragma unroll
-  for (int q = 1; q >= 0; --q) {
+  for (int q = 1; q >= 0; --q)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const int b = q == 0 ? (t & 1) * 2 + (t >> 1) * 8 : (t & 1) + (t >> 1) * 4;
-      const int s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
-      const float2 I = x[b], X = x[b + s10], Y = x[b + s01], Z = x[b + s10 + s01];
-      x[b] = make_float2(I.x + Z.x, I.y + Z.y);                             // a00 = I + Z
-      x[b + s10] = make_float2(X.x - Y.y, X.y + Y.x);                       // a10 = X + i Y
-      x[b + s01] = make_float2(X.x + Y.y, X.y - Y.x);                       // a01 = X - i Y
-      x[b + s10 + s01] = make_float2(I.x - Z.x, I.y - Z.y);                 // a11 = I - Z
+      const int b = pauli_base(q, t), s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
+      pauli_bfly_inv(x[b], x[b + s10], x[b + s01], x[b + s10 + s01]);
     }
-  }
 }
-// y = T^dagger R' T x in place (R' row-major in shared memory, read as
-// float4); the 16 products wait in this thread's shared-memory column
-// col[a * kThreads] while x is still in use, which keeps the registers of
-// both out of the same instant.
-__device__ __forceinline__ void pauli_apply(float2 x[16], const float* __restrict__ R, float2* col) {
-  pauli_fwd(x);
-#pragma unroll
-  for (int a = 0; a < 16; ++a) {
-    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int b4 = 0; b4 < 4; ++b4) {
-      const float4 r = reinterpret_cast<const float4*>(R + a * 16)[b4];
-      acc.x = fmaf(r.x, x[4 * b4].x, acc.x);
-      acc.y = fmaf(r.x, x[4 * b4].y, acc.y);
-      acc.x = fmaf(r.y, x[4 * b4 + 1].x, acc.x);
-      acc.y = fmaf(r.y, x[4 * b4 + 1].y, acc.y);
-      acc.x = fmaf(r.z, x[4 * b4 + 2].x, acc.x);
-      acc.y = fmaf(r.z, x[4 * b4 + 2].y, acc.y);
-      acc.x = fmaf(r.w, x[4 * b4 + 3].x, acc.x);
-      acc.y = fmaf(r.w, x[4 * b4 + 3].y, acc.y);
-    }
-    col[a * kThreads] = acc;
-  }
-#pragma unroll
-  for (int a = 0; a < 16; ++a) x[a] = col[a * kThreads];
-  pauli_inv(x);
-}
-// R' = T S T^dagger / 16 of a width-2 superoperator S (16 x 16 complex, shared
-// memory), one entry per thread (256 threads): row sa of T has 4 nonzeros,
-// the products of the two qubits' Pauli coefficients.
-__device__ __forceinline__ void pauli_row(int slot, int l[4], float2 coef[4]) {
+
+// R'[sa][sb] = Re sum_{l, m} T[sa][l] S[l][m] conj(T[sb][m]) / 16 of a width-2
+// superoperator S (FP64): row `slot` of T has 4 nonzeros, the products of
+// the two qubits' Pauli coefficients (I: 00 -> 1, 11 -> 1; X: 01, 10 -> 1;
+// Y: 01 -> i, 10 -> -i; Z: 00 -> 1, 11 -> -1).
+__host__ __device__ __forceinline__ void pauli_row(int slot, int l[4], int cre[4], int cim[4]) {
   const int P[2] = {((slot & 1) ? 1 : 0) | ((slot & 4) ? 2 : 0), ((slot & 2) ? 1 : 0) | ((slot & 8) ? 2 : 0)};
-  int rc[2][2][2];     // per qubit: two (r, c) pairs
-  float2 cf[2][2];     // and their coefficients
-#pragma unroll
+  int r[2][2], c[2][2], fre[2][2], fim[2][2];
   for (int j = 0; j < 2; ++j) {
-    switch (P[j]) {
-      case 0: rc[j][0][0] = 0; rc[j][0][1] = 0; rc[j][1][0] = 1; rc[j][1][1] = 1;
-              cf[j][0] = make_float2(1.f, 0.f); cf[j][1] = make_float2(1.f, 0.f); break;   // I: 00, 11
-      case 1: rc[j][0][0] = 0; rc[j][0][1] = 1; rc[j][1][0] = 1; rc[j][1][1] = 0;
-              cf[j][0] = make_float2(1.f, 0.f); cf[j][1] = make_float2(1.f, 0.f); break;   // X: 01, 10
-      case 2: rc[j][0][0] = 0; rc[j][0][1] = 1; rc[j][1][0] = 1; rc[j][1][1] = 0;
-              cf[j][0] = make_float2(0.f, 1.f); cf[j][1] = make_float2(0.f, -1.f); break;  // Y: i 01, -i 10
-      default: rc[j][0][0] = 0; rc[j][0][1] = 0; rc[j][1][0] = 1; rc[j][1][1] = 1;
-              cf[j][0] = make_float2(1.f, 0.f); cf[j][1] = make_float2(-1.f, 0.f); break;  // Z: 00, -11
-    }
+    const bool diag = P[j] == 0 || P[j] == 3;  // I, Z: entries 00 and 11; X, Y: 01 and 10
+    r[j][0] = 0; c[j][0] = diag ? 0 : 1;
+    r[j][1] = 1; c[j][1] = diag ? 1 : 0;
+    fre[j][0] = P[j] == 2 ? 0 : 1;             fim[j][0] = P[j] == 2 ? 1 : 0;
+    fre[j][1] = P[j] == 3 ? -1 : (P[j] == 2 ? 0 : 1);
+    fim[j][1] = P[j] == 2 ? -1 : 0;
   }
-#pragma unroll
   for (int u = 0; u < 2; ++u)
-#pragma unroll
     for (int v = 0; v < 2; ++v) {
-      const int r0 = rc[0][u][0], c0 = rc[0][u][1], r1 = rc[1][v][0], c1 = rc[1][v][1];
-      l[2 * u + v] = r0 + 2 * r1 + 4 * c0 + 8 * c1;
-      coef[2 * u + v] = make_float2(cf[0][u].x * cf[1][v].x - cf[0][u].y * cf[1][v].y,
-                                    cf[0][u].x * cf[1][v].y + cf[0][u].y * cf[1][v].x);
+      l[2 * u + v] = r[0][u] + 2 * r[1][v] + 4 * c[0][u] + 8 * c[1][v];
+      cre[2 * u + v] = fre[0][u] * fre[1][v] - fim[0][u] * fim[1][v];
+      cim[2 * u + v] = fre[0][u] * fim[1][v] + fim[0][u] * fre[1][v];
     }
 }
-__device__ __forceinline__ void pauli_transform(const float2* sS, float* R) {
-  const int sa = threadIdx.x / 16, sb = threadIdx.x % 16;
-  int la[4], lb[4];
-  float2 ca[4], cb[4];
-  pauli_row(sa, la, ca);
-  pauli_row(sb, lb, cb);
-  float acc = 0.f;  // Re sum_{u,v} ca[u] S[la[u]][lb[v]] conj(cb[v])
-#pragma unroll
+__host__ __device__ __forceinline__ double pauli_entry(const double2* S, int sa, int sb) {
+  int la[4], lb[4], ar[4], ai[4], br[4], bi[4];
+  pauli_row(sa, la, ar, ai);
+  pauli_row(sb, lb, br, bi);
+  double acc = 0.0;
   for (int u = 0; u < 4; ++u)
-#pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const float2 sv = sS[la[u] * 16 + lb[v]];
-      const float2 t = make_float2(ca[u].x * sv.x - ca[u].y * sv.y, ca[u].x * sv.y + ca[u].y * sv.x);
-      acc += t.x * cb[v].x + t.y * cb[v].y;  // Re (t conj(cb))
+      const double2 sv = S[la[u] * 16 + lb[v]];
+      const double tr = ar[u] * sv.x - ai[u] * sv.y, ti = ar[u] * sv.y + ai[u] * sv.x;  // T[sa][l] S[l][m]
+      acc += tr * br[v] + ti * bi[v];                                                // Re (t conj(T[sb][m]))
     }
-  R[sa * 16 + sb] = acc * (1.f / 16.f);
+  return acc * (1.0 / 16.0);
+}
+// Whether a width-2 tile-item block takes the Pauli row lists: FP64 when they
+// cost fewer FP64 operations per group (2 per nonzero + 128 adds against 4
+// per nonzero of S's row lists); split (dense S otherwise) when R' has at
+// most half its entries.
+__host__ __device__ __forceinline__ bool pauli_better(int prec, int nnzS, int nnzR) {
+  return prec == 0 ? (2 * nnzR + 128 < 4 * nnzS) : (nnzR <= 128);
 }
 
 // One canonical group of a width-K split block on the shared-memory copy of
@@ -383,7 +384,7 @@ __device__ __forceinline__ void apply_group_lists_resident(double2* sR, unsigned
 // One canonical 16 x 16 tile u of a width-K split block (see Tile16).
 template <int K>
 __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, const ApplyParams& p,
-                                             const float2* sS, const Tile16& t, const float* ptm, float2* col) {
+                                             const float2* sS, const Tile16& t) {
   constexpr int D = 1 << (2 * K);
   // a warp covers 8 row rests x 4 column rests (full 32-byte sectors in both
   // orientations)
@@ -405,17 +406,11 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
     if (!up) v.y = -v.y;
     x[l] = v;
   }
-  if constexpr (K == 2) pauli_apply(x, ptm, col);  // y = S x in the Pauli basis
 #pragma unroll
   for (int o = 0; o < D; ++o) {
-    float2 acc;
-    if constexpr (K == 2) {
-      acc = x[o];
-    } else {
-      acc = make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int l = 0; l < D; ++l) Cx<float2>::fma(acc, sS[o * D + l], x[l]);
-    }
+    for (int l = 0; l < D; ++l) Cx<float2>::fma(acc, sS[o * D + l], x[l]);
     const unsigned r = rbase + t.rt[o], c = cbase + t.ct[o];
     if (r <= c) {
       rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
@@ -426,13 +421,139 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
   }
 }
 
+// The same tile walk for a width-2 block in the Pauli basis: the entries
+// are transformed in registers, parked in this thread's shared-memory column
+// col[slot * kThreads] for the row-list products (real R' values in val),
+// transformed back and stored.
+__device__ __forceinline__ void apply_tile16_pauli(float2* rho, unsigned long long u, const ApplyParams& p,
+                                                   const float* val, const RowLists& rl, const Tile16& t,
+                                                   float2* col) {
+  constexpr int D = 16;
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int i = (lane % 8) + 8 * (w % 2), j = (lane / 8) + 4 * (w / 2);
+  bool diag = false;
+  const unsigned long long tt = canonical_group(u, 32, &diag);
+  if (diag && i > j) return;
+  const bool self = diag && i == j;
+  const unsigned rbase = (unsigned)deposit_zeros((tt & 0xffffffffull) * 16, t.qs, 2) + t.dep16[i];
+  const unsigned cbase = (unsigned)deposit_zeros((tt >> 32) * 16, t.qs, 2) + t.dep16[j];
+  float2 x[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const unsigned r = rbase + t.rt[l], c = cbase + t.ct[l];
+    const bool up = r <= c;
+    float2 v = __ldcg(&rho[up ? ((unsigned long long)r | ((unsigned long long)c << p.n))
+                              : ((unsigned long long)c | ((unsigned long long)r << p.n))]);
+    if (!up) v.y = -v.y;
+    x[l] = v;
+  }
+  pauli_fwd(x);
+#pragma unroll
+  for (int a = 0; a < D; ++a) col[a * kThreads] = x[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = rl.rowptr[a]; k < rl.rowptr[a + 1]; ++k) {
+      const float v = val[k];
+      const float2 xc = col[rl.col[k] * kThreads];
+      acc.x = fmaf(v, xc.x, acc.x);
+      acc.y = fmaf(v, xc.y, acc.y);
+    }
+    x[a] = acc;
+  }
+  pauli_inv(x);
+#pragma unroll
+  for (int o = 0; o < D; ++o) {
+    float2 acc = x[o];
+    const unsigned r = rbase + t.rt[o], c = cbase + t.ct[o];
+    if (r <= c) {
+      rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+    } else if (!self) {
+      acc.y = -acc.y;
+      rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+    }
+  }
+}
+
+// FP64 tile items of a width-2 block in the Pauli basis: the group's entries
+// gathered into this thread's shared-memory column (as the row-list path
+// does), transformed there, multiplied by the real R' row lists into
+// registers, transformed back and written in place.
+__device__ __forceinline__ void apply_group_pauli_global(double2* rho, unsigned long long t, const ApplyParams& p,
+                                                         const double* val, const RowLists& rl, double2* mine) {
+  constexpr int D = 16;
+  bool self = false;
+  unsigned long long base = canonical_group(t, p.n - 2, &self);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const unsigned long long low = base & ((1ull << p.pos[i]) - 1ull);
+    base = ((base >> p.pos[i]) << (p.pos[i] + 1)) | low;
+  }
+  const unsigned int rmask = (1u << p.n) - 1u;
+  const unsigned int rb = (unsigned int)(base & rmask), cb = (unsigned int)(base >> p.n);
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const unsigned int r = rb + (unsigned int)(p.off[l] & rmask), c = cb + (unsigned int)(p.off[l] >> p.n);
+    const bool conj = r > c;
+    double2 v = __ldcg(&rho[conj ? ((unsigned long long)c | ((unsigned long long)r << p.n))
+                                 : ((unsigned long long)r | ((unsigned long long)c << p.n))]);
+    if (conj) v.y = -v.y;
+    mine[l * kThreads] = v;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int tb = 0; tb < 4; ++tb) {
+      const int b = pauli_base(q, tb), s10 = q == 0 ? 1 : 2, s01 = q == 0 ? 4 : 8;
+      double2 a00 = mine[b * kThreads], a10 = mine[(b + s10) * kThreads], a01 = mine[(b + s01) * kThreads],
+              a11 = mine[(b + s10 + s01) * kThreads];
+      pauli_bfly_fwd(a00, a10, a01, a11);
+      mine[b * kThreads] = a00;
+      mine[(b + s10) * kThreads] = a10;
+      mine[(b + s01) * kThreads] = a01;
+      mine[(b + s10 + s01) * kThreads] = a11;
+    }
+  double2 y[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = rl.rowptr[a]; k < rl.rowptr[a + 1]; ++k) {
+      const double v = val[k];
+      const double2 xc = mine[rl.col[k] * kThreads];
+      acc.x = ::fma(v, xc.x, acc.x);
+      acc.y = ::fma(v, xc.y, acc.y);
+    }
+    y[a] = acc;
+  }
+  pauli_inv(y);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double2 acc = y[i];
+    const unsigned int r = rb + (unsigned int)(p.off[i] & rmask), c = cb + (unsigned int)(p.off[i] >> p.n);
+    if (r <= c) {
+      rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+    } else if (!self) {
+      acc.y = -acc.y;
+      rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+    }
+  }
+}
+
 // Copy a block's descriptor to shared memory with its superoperator: dense
 // (split) or as row lists (FP64; zero tests on the bit patterns, so -0.0
 // counts as zero). The row lists take rows in order, each thread i < D
 // placing row i after the counts of rows < i.
+// Shared state of the Pauli-basis decision of a staged block.
+struct PauliStage {
+  double R[256];       // R' of a width-2 block, FP64
+  double thr;          // structural-zero threshold
+  unsigned short mask[16];
+  int on;              // the staged block takes the Pauli row lists
+};
+
 template <typename T2>
 __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl, Tile16* t16,
-                                            float* ptm) {
+                                            PauliStage* ps, bool allow_pauli) {
   static_assert(sizeof(BBlk) % 8 == 0 && sizeof(BBlk) / 8 <= kThreads, "descriptor copied one word per thread");
   if (threadIdx.x < sizeof(BBlk) / 8)  // in parallel: one 8-byte word per thread
     reinterpret_cast<unsigned long long*>(s_blk)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(blk)[threadIdx.x];
@@ -462,10 +583,6 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
         t16->ct[threadIdx.x] = ct;
       }
     }
-    if (K == 2) {  // the Pauli-basis matrix R' of the block (split width 2)
-      __syncthreads();
-      pauli_transform(reinterpret_cast<const float2*>(sS), ptm);
-    }
   } else {
     const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(S);
     unsigned int m = 0;
@@ -490,6 +607,51 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
         }
     }
   }
+  if (threadIdx.x == 0) ps->on = 0;
+  __syncthreads();
+  if (!allow_pauli || s_blk->p.width != 2) return;
+  // tile items of width-2 blocks: R' in FP64, structural zeros dropped, and
+  // the Pauli row lists replace S's when they cost less (pauli_better)
+  ps->R[threadIdx.x] = pauli_entry(s_blk->S64, threadIdx.x / 16, threadIdx.x % 16);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < 256; e += 32) mx = fmax(mx, fabs(ps->R[e]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) ps->thr = mx * kPauliZeroRel;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    unsigned m = 0;
+    for (int j = 0; j < 16; ++j)
+      if (fabs(ps->R[threadIdx.x * 16 + j]) > ps->thr) m |= 1u << j;
+    ps->mask[threadIdx.x] = (unsigned short)m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nnzR = 0;
+    for (int i = 0; i < 16; ++i) nnzR += __popc(ps->mask[i]);
+    const int nnzS = sizeof(T2) == 16 ? rl->rowptr[16] : 256;
+    ps->on = pauli_better(sizeof(T2) == 16 ? 0 : 1, nnzS, nnzR) ? 1 : 0;
+    if (ps->on) {
+      rl->rowptr[0] = 0;
+      for (int i = 0; i < 16; ++i) rl->rowptr[i + 1] = rl->rowptr[i] + __popc(ps->mask[i]);
+    }
+  }
+  __syncthreads();
+  if (ps->on && threadIdx.x < 16) {
+    int k = rl->rowptr[threadIdx.x];
+    for (int j = 0; j < 16; ++j)
+      if ((ps->mask[threadIdx.x] >> j) & 1u) {
+        const double v = ps->R[threadIdx.x * 16 + j];
+        if (sizeof(T2) == 16)
+          reinterpret_cast<double*>(sS)[k] = v;
+        else
+          reinterpret_cast<float*>(sS)[k] = (float)v;
+        rl->col[k] = (unsigned char)j;
+        ++k;
+      }
+  }
   __syncthreads();
 }
 
@@ -508,7 +670,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
   __shared__ BBlk s_blk;
   __shared__ RowLists s_rl;
   __shared__ Tile16 s_t16;
-  __shared__ __align__(16) float s_ptm[256];  // Pauli-basis matrix of a split width-2 block
+  __shared__ PauliStage s_ps;  // Pauli-basis decision and R' of the staged block
   __shared__ int s_idx;
   constexpr bool kF64 = sizeof(T2) == 16;
   for (;;) {
@@ -526,7 +688,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       const int N = 1 << (2 * n);
       for (int e = threadIdx.x; e < N; e += blockDim.x) sR[e] = Cx<T2>::ldcg(&rho[e]);
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
-        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16, s_ptm);
+        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16, &s_ps, false);
         const ApplyParams& p = s_blk.p;
         for (unsigned long long g = threadIdx.x; g < p.n_canon; g += blockDim.x) {
           if constexpr (kF64) {
@@ -551,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
     }
     // tile item: stage the block (independent of earlier blocks), then wait
     // until every tile of the previous block of this job is done
-    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16, s_ptm);
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16, &s_ps, true);
     if (threadIdx.x == 0 && it.block > 0) {
       const int need = jb.never_ready ? 0x7fffffff : s_blk.tile_prefix;
       long long spins = 0;
@@ -580,6 +742,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
           if (p.width == 1)
             apply_group_lists_global<1, true>(rho64, g, p, val, s_rl, mine);
+          else if (s_ps.on)
+            apply_group_pauli_global(rho64, g, p, reinterpret_cast<const double*>(sS), s_rl, mine);
           else
             apply_group_lists_global<2, true>(rho64, g, p, val, s_rl, mine);
         }
@@ -594,9 +758,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
           // the resident buffer is free in tile items: one column per thread
           float2* col = reinterpret_cast<float2*>(sR) + threadIdx.x;
           if (p.width == 1)
-            apply_tile16<1>(rho, u, p, sS, s_t16, s_ptm, col);
+            apply_tile16<1>(rho, u, p, sS, s_t16);
+          else if (s_ps.on)
+            apply_tile16_pauli(rho, u, p, reinterpret_cast<const float*>(sS), s_rl, s_t16, col);
           else
-            apply_tile16<2>(rho, u, p, sS, s_t16, s_ptm, col);
+            apply_tile16<2>(rho, u, p, sS, s_t16);
         }
       }
     }

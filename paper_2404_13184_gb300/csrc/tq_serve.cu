@@ -82,7 +82,7 @@ struct Req {
   HostTables t;
   size_t rho_off = 0, rho_bytes = 0;
   size_t tab_off = 0, tab_bytes = 0;
-  size_t o_sops = 0, o_sb = 0;  // within the table allocation
+  size_t o_sops = 0, o_sb = 0, o_sb64 = 0;  // within the table allocation
   int next_block = 0;
   int state = 0;  // 0 queued, 1 live, 2 done
   double result[2 + 16] = {};
@@ -182,6 +182,7 @@ size_t table_layout(int prec, Req& r) {
   r.o_sops = off;
   off = align_up(off + r.t.sop_entries * sizeof(double2), 256);
   const size_t o_sb64 = off;
+  r.o_sb64 = o_sb64;
   off = align_up(off + r.t.sb_entries * sizeof(double2), 256);
   r.o_sb = prec == TQ_FP64 ? o_sb64 : off;
   if (prec == TQ_SPLIT) off = align_up(off + r.t.sb_entries * sizeof(float2), 256);
@@ -408,11 +409,13 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
     for (size_t m = 0; m < r.masks.size(); ++m) j.masks[m] = r.masks[m];
     const size_t esz = s->prec == TQ_FP64 ? sizeof(double2) : sizeof(float2);
     const char* sb = static_cast<const char*>(s->tab_mem.ptr) + r.tab_off + r.o_sb;
+    const double2* sb64 = reinterpret_cast<const double2*>(static_cast<const char*>(s->tab_mem.ptr) + r.tab_off + r.o_sb64);
     for (int b = r.next_block; b < r.next_block + cnt; ++b) {
       BBlk bb;
       std::memset(&bb, 0, sizeof(bb));
       bb.p = r.prog.params[b];
       bb.S = sb + (size_t)r.prog.sb_off[b] * esz;
+      bb.S64 = sb64 + r.prog.sb_off[b];
       blks.push_back(bb);
     }
     set_tiles(blks.data() + j.block0, cnt, j.tile_log2, j.herm != 0, tiled16_job(r.n, s->prec));

@@ -49,25 +49,87 @@ def test_batch_matches_oracle_and_replays(tq, precision):
     b.free()
 
 
+def _block_superops(tq, n, ops, width, precision):
+    """(width, superoperator) of every fused block, composed with numpy from
+    the library's gate matrices in the planner's blocks (local order: the
+    qubits as they first appear; local index r + 2^w c, bit j = qubit j)."""
+    block_of, widths = tq.plan_fusion(n, ops, width, precision)
+    out = []
+    for b, w in enumerate(widths):
+        members = [ops[i] for i in range(len(ops)) if block_of[i] == b]
+        qs = []
+        for _, q, _ in members:
+            for v in q:
+                if v not in qs:
+                    qs.append(v)
+        D = 4 ** w
+        S = np.eye(D, dtype=complex)
+        for name, q, params in members:
+            U = tq.gate_matrix(name, params)
+            k = len(q)
+            So = np.kron(U.conj(), U)                     # local index r + 2^k c of the op
+            pos = [qs.index(v) for v in q]
+            E = np.zeros((D, D), dtype=complex)
+            for i in range(D):
+                for j in range(D):
+                    if any(((i >> t) & 1) != ((j >> t) & 1) or ((i >> (w + t)) & 1) != ((j >> (w + t)) & 1)
+                           for t in range(w) if t not in pos):
+                        continue
+                    li = sum((((i >> pos[t]) & 1) << t) | (((i >> (pos[t] + w)) & 1) << (k + t)) for t in range(k))
+                    lj = sum((((j >> pos[t]) & 1) << t) | (((j >> (pos[t] + w)) & 1) << (k + t)) for t in range(k))
+                    E[i, j] = So[li, lj]
+            S = E @ S
+        out.append((w, S))
+    return out
+
+
+def _pauli_nonzeros(S):
+    """Nonzeros of R' = T S T^dagger / 16 (the Pauli-basis matrix the batch
+    kernel builds for width-2 blocks), entries at most 2^-47 of the largest
+    dropped as the kernel does."""
+    t1 = {0: {(0, 0): 1, (1, 1): 1}, 1: {(0, 1): 1, (1, 0): 1}, 2: {(0, 1): 1j, (1, 0): -1j},
+          3: {(0, 0): 1, (1, 1): -1}}
+    T = np.zeros((16, 16), dtype=complex)
+    for P0 in range(4):
+        for P1 in range(4):
+            slot = [0, 1, 4, 5][P0] + [0, 2, 8, 10][P1]
+            for l in range(16):
+                r0, r1, c0, c1 = l & 1, (l >> 1) & 1, (l >> 2) & 1, (l >> 3) & 1
+                T[slot, l] = t1[P0].get((r0, c0), 0) * t1[P1].get((r1, c1), 0)
+    R = (T @ S @ T.conj().T).real / 16
+    return int(np.sum(np.abs(R) > np.max(np.abs(R)) * 2.0 ** -47))
+
+
 def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
     """Flops and HBM bytes tq_batch_work must report for one job, from the
-    plan's block widths: every job runs its canonical groups (Hermitian
-    mode); FP64 counts nonzeros (a diagonal block has D of them)."""
+    plan's blocks: every job runs its canonical groups (Hermitian mode);
+    FP64 counts nonzeros (a diagonal block has D of them), split counts all;
+    width-2 blocks of tile jobs that the kernel runs in the Pauli basis count
+    4 per nonzero of R' plus 128 (FP64 when that is cheaper than 4 per
+    nonzero of S, split when R' has at most 128 nonzeros)."""
     esz = 16 if precision == "fp64" else 8
     resident = esz * 4 ** n <= 64 * 1024
     herm = True
-    _, widths = tq.plan_fusion(n, ops, width, precision)
     flops = bytes_ = 0
-    for w in widths:
+    for w, S in _block_superops(tq, n, ops, width, precision):
         M = 2 ** (n - w)
         groups = M * (M + 1) // 2 if herm else 4 ** (n - w)
         nnz = 4 ** w if (precision == "fp64" and diagonal_fp64) else 16 ** w
-        flops += 8 * nnz * groups
+        per = 8 * nnz
+        if not resident and w == 2:
+            nr = _pauli_nonzeros(S)
+            if (2 * nr + 128 < 4 * nnz) if precision == "fp64" else (nr <= 128):
+                per = 4 * nr + 128
+        flops += per * groups
         if not resident:
             bytes_ += ((4 ** n + 2 ** n) if herm else 2 * 4 ** n) * esz
-    if resident and widths:
+    if resident and widths_nonempty(tq, n, ops, width, precision):
         bytes_ += 2 * 4 ** n * esz
     return flops, bytes_
+
+
+def widths_nonempty(tq, n, ops, width, precision):
+    return len(tq.plan_fusion(n, ops, width, precision)[1]) > 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split"])
