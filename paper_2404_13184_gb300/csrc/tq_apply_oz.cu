@@ -13,7 +13,8 @@
 // Fixed-point slicing. Every operand value is cut into seven balanced 8-bit
 // digits of a fixed-point number aligned to a shared exponent: for group m
 // the largest biased exponent E_m of its 32 values, for output row n of R
-// the largest biased exponent G_n of the row. With F the value's 53-bit
+// the largest biased exponent G_n of the row (both at least 64: a group or
+// row whose largest entry is below 2^-959, or is zero, is aligned to 2^-959). With F the value's 53-bit
 // significand shifted to that alignment and rounded to nearest (54 bits,
 // F < 2^54),
 //     |v| ~ F * 2^(E - 1076),   F = sum_i d_i 2^(8 (6 - i)),  -128 <= d_i < 128,
@@ -21,7 +22,8 @@
 // minus 128 (the added 128s carry exactly where a byte is >= 128; the top
 // byte stays below 192, so nothing is lost). A digit is an integer, exact in
 // FP16, and enters the tensor cores as such (the value's sign applied to
-// all its digits). Then
+// all its digits; a conjugated entry's imaginary sign flipped there too, so
+// no FP64 instruction touches the operands). Then
 //     Y[m][n] ~ 2^(E_m + G_n - 2152) sum_t 2^(8 (12 - t)) P_t,
 //     P_t = sum_{i + j = t} sum_k A_i[m][k] B_j[n][k],
 // P_t an integer with |P_t| <= 7 * 32 * 128^2 < 2^22: every partial sum is
@@ -50,11 +52,12 @@
 // groups (128 groups), with two threads per group in a CTA of 256 threads,
 // each taking 8 of the group's 16 entries and 8 of its 16 outputs. Per unit
 // a thread issues the loads of its next group half into registers, slices
-// its current half into the eight digit operands (A_0..A_7, 8 KB each in
-// shared memory), and after a CTA barrier one thread issues the 16 MMAs (8 pairs x two K-halves, M = 128, N = 32, K = 16) into 7 accumulators
-// of 32 tensor-memory columns and commits them to an mbarrier; every thread
-// waits (bounded), reads its part of its row of the accumulators and writes
-// its 8 outputs.
+// its current half into the seven digit operands (A_0..A_6, 8 KB each in
+// shared memory), and after a CTA barrier one thread issues the 14 MMAs (7
+// A digits x two K-halves, M = 128, N = 32 (8 - i), K = 16) into the 8
+// accumulators of 32 tensor-memory columns and commits them to an mbarrier;
+// every thread waits (bounded), reads its part of its row of the
+// accumulators and writes its 8 outputs.
 //
 // Width-1 blocks run through the same kernel as a width-2 block with the
 // identity on a second qubit (S (x) I, built while slicing R), which moves
@@ -94,53 +97,61 @@ constexpr uint32_t kTmemCols = 256;
 constexpr int kCtasPerSm = 2;
 
 // F + 0x0080808080808080 for v's significand aligned to biased exponent E
-// (v's exponent <= E): shifted right by E - e_v and rounded to nearest
-// (ties away from zero), F < 2^54. Byte 6 - i of the result, minus 128, is
-// digit i. Zeros and subnormals (exponent field 0) give F = 0 (every byte
-// 0x80).
+// (E >= v's exponent and E >= 64): with M2 the 53-bit significand (implicit
+// bit set) times 4 and sh = E - e_v, T = M2 >> sh = floor(M / 2^(sh - 1))
+// (PTX clamps shift amounts above 64, giving 0), and F = (T + 1) >> 1 is
+// M / 2^sh rounded to nearest with ties away from zero (F < 2^54); the
+// offset goes in before the last shift (2 * offset + 1 = 0x0101010101010101).
+// Zeros and subnormals (exponent field 0) have sh >= 64 and give F = 0.
+// Byte 6 - i of the result, minus 128, is digit i.
 __device__ __forceinline__ unsigned long long aligned_offset(uint32_t hi, uint32_t lo, int E) {
-  const int ev = (int)((hi >> 20) & 0x7ffu);
-  const int sh = E - ev;
-  const unsigned long long M1 = (((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) << 1;
-  const unsigned long long F =
-      (ev == 0 || sh > 54) ? 0ull : sh == 0 ? M1 : (((M1 >> (sh - 1)) + 1ull) >> 1);
-  return F + 0x0080808080808080ull;
+  const uint32_t sh = (uint32_t)(E - (int)((hi >> 20) & 0x7ffu));
+  const unsigned long long M2 = (((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) << 2;
+  unsigned long long T;
+  asm("shr.b64 %0, %1, %2;" : "=l"(T) : "l"(M2), "r"(sh));
+  return (T + 0x0101010101010101ull) >> 1;
 }
 
 __device__ __forceinline__ uint32_t abs_hi(double v) { return (uint32_t)__double2hiint(v) & 0x7fffffffu; }
 
 // FP16x2 word of digit I of a complex entry (low half: Re, high half: Im):
 // the two digit bytes are placed in the low mantissa bytes of FP16 1024
-// (0x6400), so each half reads 1024 + byte; subtracting 1152 = 1024 + 128
-// leaves byte - 128 exactly; the entry's signs are applied last.
+// (0x6400), so each half reads 1024 + byte; one FP16 multiply-add by the
+// half's sign s (+-1) and -1152 s leaves s (byte - 128) exactly (every
+// intermediate is an integer below 2^11).
 template <int I>
-__device__ __forceinline__ uint32_t digit_pair(unsigned long long fr, unsigned long long fi, uint32_t sign) {
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long fr, unsigned long long fi, uint32_t sgn,
+                                               uint32_t nsg) {
   constexpr int k = 6 - I;  // byte of F + offset
   const uint32_t r = k >= 4 ? (uint32_t)(fr >> 32) : (uint32_t)fr;
   const uint32_t i = k >= 4 ? (uint32_t)(fi >> 32) : (uint32_t)fi;
   const uint32_t w = (__byte_perm(r, i, (uint32_t)((k % 4) | ((4 + k % 4) << 8))) & 0x00ff00ffu) | 0x64006400u;
   uint32_t d;
-  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(w), "r"(0x64806480u));
-  return d ^ sign;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(w), "r"(sgn), "r"(nsg));
+  return d;
 }
 
 // Stores the digit words of 4 consecutive complex entries (one 16-byte chunk
-// of every digit operand's row).
-__device__ __forceinline__ void store_chunk(const double2 x[4], int E, uint32_t row_chunk, uint32_t digit_bytes) {
+// of every digit operand's row); bit e of conj: entry e is conjugated (its
+// imaginary sign flipped in the digits).
+__device__ __forceinline__ void store_chunk(const double2 x[4], uint32_t conj, int E, uint32_t row_chunk,
+                                            uint32_t digit_bytes) {
   uint32_t w[kDigits][4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const uint32_t rh = (uint32_t)__double2hiint(x[e].x), rl = (uint32_t)__double2loint(x[e].x);
     const uint32_t ih = (uint32_t)__double2hiint(x[e].y), il = (uint32_t)__double2loint(x[e].y);
     const unsigned long long fr = aligned_offset(rh, rl, E), fi = aligned_offset(ih, il, E);
-    const uint32_t sign = ((rh & 0x80000000u) >> 16) | (ih & 0x80000000u);  // FP16 sign bits of both halves
-    w[0][e] = digit_pair<0>(fr, fi, sign);
-    w[1][e] = digit_pair<1>(fr, fi, sign);
-    w[2][e] = digit_pair<2>(fr, fi, sign);
-    w[3][e] = digit_pair<3>(fr, fi, sign);
-    w[4][e] = digit_pair<4>(fr, fi, sign);
-    w[5][e] = digit_pair<5>(fr, fi, sign);
-    w[6][e] = digit_pair<6>(fr, fi, sign);
+    // FP16 sign bits of both halves
+    const uint32_t sign = ((rh & 0x80000000u) >> 16) | ((ih ^ (((conj >> e) & 1u) << 31)) & 0x80000000u);
+    const uint32_t sgn = 0x3c003c00u ^ sign, nsg = 0xe480e480u ^ sign;  // FP16 +-1 and -+1152 per half
+    w[0][e] = digit_pair<0>(fr, fi, sgn, nsg);
+    w[1][e] = digit_pair<1>(fr, fi, sgn, nsg);
+    w[2][e] = digit_pair<2>(fr, fi, sgn, nsg);
+    w[3][e] = digit_pair<3>(fr, fi, sgn, nsg);
+    w[4][e] = digit_pair<4>(fr, fi, sgn, nsg);
+    w[5][e] = digit_pair<5>(fr, fi, sgn, nsg);
+    w[6][e] = digit_pair<6>(fr, fi, sgn, nsg);
   }
 #pragma unroll
   for (int i = 0; i < kDigits; ++i) sts128(row_chunk + i * digit_bytes, w[i][0], w[i][1], w[i][2], w[i][3]);
@@ -173,9 +184,9 @@ __device__ __forceinline__ void build_b_digits(unsigned char* smem, uint32_t sba
   }
   mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
   mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-  const int G = (int)(mx >> 20);
+  const int G = max((int)(mx >> 20), 64);
   if (quarter == 0) reinterpret_cast<int*>(smem + kOffG)[n] = G;
-  store_chunk(r, G, sbase + kOffB + core_off(n, quarter), kBTermBytes);
+  store_chunk(r, 0u, G, sbase + kOffB + core_off(n, quarter), kBTermBytes);
   // the zero slab B_7: digit 0's MMA reaches it and clears accumulator block 7
   sts128(sbase + kOffB + kDigits * kBTermBytes + core_off(n, quarter), 0u, 0u, 0u, 0u);
 }
@@ -204,8 +215,11 @@ __host__ __device__ constexpr unsigned long long magic_offset() {
 
 // Real output from its 8 accumulator values (orders 0..7): Z = sum_t P_t
 // 2^(8 (5 - t)) (orders 6 and 7 rounded) as the FP64 number Z * 2^scale
-// (scale = E + G - 2096), built from Z's bits with integer operations.
-__device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
+// (scale = E + G - 2096), built from Z's bits with integer operations; neg
+// (0 or 2^31) flips the result's sign. The magic patterns' sum is taken out
+// by starting Z at its negative (mod 2^64).
+__device__ __forceinline__ double recombine(const float c[kAccs], int scale, uint32_t neg) {
+  constexpr unsigned long long kZ0 = 0ull - magic_offset();
   const float m0 = __uint_as_float(magic_bits(0));
   const uint32_t b0 = __float_as_uint(c[0] + m0);
   const uint32_t b1 = __float_as_uint(c[1] + m0);
@@ -215,12 +229,14 @@ __device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
   const uint32_t b5 = __float_as_uint(c[5] + m0);
   const uint32_t b6 = __float_as_uint(c[6] + __uint_as_float(magic_bits(-8)));   // rounded to units of 2^8
   const uint32_t b7 = __float_as_uint(c[7] + __uint_as_float(magic_bits(-16)));  // rounded to units of 2^16
-  unsigned long long Z = (unsigned long long)(b0 * 256u + b1) << 32;  // wraps mod 2^64 like the rest
+  // wraps mod 2^64 like the rest
+  unsigned long long Z = ((unsigned long long)(b0 * 256u + b1 + (uint32_t)(kZ0 >> 32)) << 32) | (uint32_t)kZ0;
   Z = mad_wide(b2, 1u << 24, Z);
   Z = mad_wide(b3, 1u << 16, Z);
   Z = mad_wide(b4, 1u << 8, Z);
-  Z += (unsigned long long)b5 + b6 + b7;
-  Z -= magic_offset();
+  Z = mad_wide(b5, 1u, Z);
+  Z = mad_wide(b6, 1u, Z);
+  Z = mad_wide(b7, 1u, Z);
   // |Z| normalised to bit 63, rounded to 53 bits (a carry into bit 53 lands
   // in the exponent field), placed under the biased exponent 1086 - lz +
   // scale; zero and results below the normal range give 0
@@ -232,7 +248,8 @@ __device__ __forceinline__ double recombine(const float c[kAccs], int scale) {
   const unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);
   const int eb = 1085 - lz + scale;  // biased exponent - 1 (mant carries the leading 1)
   if (eb < 0) return 0.0;
-  return __longlong_as_double((long long)((sm & 0x8000000000000000ull) + ((unsigned long long)eb << 52) + mant));
+  return __longlong_as_double(
+      (long long)((((sm & 0x80000000ull) ^ neg) << 32) + ((unsigned long long)eb << 52) + mant));
 }
 
 struct Group {
@@ -241,7 +258,7 @@ struct Group {
 };
 
 // Accumulator values of this thread's 8 real outputs n0 .. n0 + 7 (columns
-// n0.. of each of the 7 accumulators), all loads issued before one wait.
+// n0.. of each of the 8 accumulators), all loads issued before one wait.
 __device__ __forceinline__ void load_accs(uint32_t t_row, int n0, uint32_t r[kAccs][8]) {
 #pragma unroll
   for (int a = 0; a < kAccs; ++a)
@@ -325,13 +342,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
   };
   // this thread's half of the group: entries 8 h .. 8 h + 7, i.e. local
   // entries l < 8 from a column base that includes bit 3 (stored copies;
-  // those read from their transposes are conjugated at use)
+  // those read from their transposes are conjugated in the digits). A
+  // group below the diagonal of a diagonal tile (not canonical) reads its
+  // in-range entries too; its outputs are never written.
   auto load = [&](const Group& g, double2 x[H]) {
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       bool up;
-      const unsigned int idx = entry_index(g.rb, g.cb, l, b0, b1, N, &up);
-      x[l] = g.active ? rho[idx] : make_double2(0.0, 0.0);
+      x[l] = rho[entry_index(g.rb, g.cb, l, b0, b1, N, &up)];
     }
   };
 
@@ -353,19 +371,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
       gn = group_of(u + gridDim.x);
       load(gn, xn);
     }
-    uint32_t mx = 0;
+    uint32_t mx = 0, conj = 0;
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       bool up;
       (void)entry_index(g.rb, g.cb, l, b0, b1, N, &up);
-      if (!up) x[l].y = -x[l].y;
+      conj |= (up ? 0u : 1u) << l;
       mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
     }
     s_E[tid] = mx;
     __syncthreads();  // both halves' maxima (and the previous unit's TMEM reads are done)
-    const int E = (int)(max(mx, s_E[tid ^ 128]) >> 20);
+    const int E = max((int)(max(mx, s_E[tid ^ 128]) >> 20), 64);
 #pragma unroll
-    for (int c = 0; c < 2; ++c) store_chunk(x + 4 * c, E, a_row + c * 128u, kADigitBytes);
+    for (int c = 0; c < 2; ++c) store_chunk(x + 4 * c, conj >> (4 * c), E, a_row + c * 128u, kADigitBytes);
     fence_operands();
     fence_before_sync();
     __syncthreads();
@@ -408,17 +426,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
           cr[a] = __uint_as_float(cv[a][2 * e]);
           ci[a] = __uint_as_float(cv[a][2 * e + 1]);
         }
-        double2 y;
-        y.x = recombine(cr, E + s_G[2 * o] - 2096);
-        y.y = recombine(ci, E + s_G[2 * o + 1] - 2096);
         bool up;
         const unsigned int idx = entry_index(g.rb, g.cb, 4 * ch + e, b0, b1, N, &up);
-        if (up) {
-          rho[idx] = y;
-        } else if (!g.self) {  // a self-conjugate group writes its upper entries only
-          y.y = -y.y;
-          rho[idx] = y;
-        }
+        double2 y;
+        y.x = recombine(cr, E + s_G[2 * o] - 2096, 0u);
+        y.y = recombine(ci, E + s_G[2 * o + 1] - 2096, up ? 0u : 0x80000000u);  // conjugated below the diagonal
+        if (up || !g.self) rho[idx] = y;  // a self-conjugate group writes its upper entries only
       }
     }
     fence_before_sync();

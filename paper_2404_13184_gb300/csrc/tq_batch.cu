@@ -72,8 +72,9 @@ int default_tile_log2(int n, int prec) {
 
 // Algorithmic flops and HBM bytes of one run (see tq_batch_work): one CTA
 // per job, threads over its blocks; FP64 counts the nonzeros of S by their
-// bit patterns, as the row-list staging does, and width-2 blocks of tile
-// jobs make the kernel's Pauli-basis choice (pauli_better on the same R').
+// bit patterns, as the row-list staging does, and FP64 width-2 blocks of
+// tile jobs make the kernel's Pauli-basis choice (pauli_better on the same
+// R').
 __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restrict__ blks, int prec,
                              unsigned long long* __restrict__ out) {
   const BJob& jb = jobs[blockIdx.x];
@@ -93,7 +94,7 @@ __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restri
     // of them), or in the Pauli basis 4 per real-times-complex multiply-add
     // plus the 128 adds of the two basis changes
     unsigned long long per = 8ull * nnz;
-    if (!jb.resident && bk.p.width == 2) {
+    if (prec == 0 && !jb.resident && bk.p.width == 2) {
       double Rp[256], mx = 0.0;
       for (int e = 0; e < 256; ++e) {
         Rp[e] = pauli_entry(bk.S64, e / 16, e % 16);
@@ -102,7 +103,7 @@ __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restri
       const double thr = mx * kPauliZeroRel;
       int nnzR = 0;
       for (int e = 0; e < 256; ++e) nnzR += fabs(Rp[e]) > thr;
-      if (pauli_better(prec, (int)nnz, nnzR)) per = 4ull * nnzR + 128;
+      if (pauli_better((int)nnz, nnzR)) per = 4ull * nnzR + 128;
     }
     const unsigned long long groups = jb.herm ? bk.p.n_canon : bk.p.n_groups;
     fl += per * groups;

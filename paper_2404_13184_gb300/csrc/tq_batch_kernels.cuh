@@ -41,7 +41,7 @@ struct BJob {
 struct BBlk {
   ApplyParams p;
   const void* S;       // fused superoperator, 4^w x 4^w row-major (double2 or float2)
-  const double2* S64;  // the same in FP64 (both precisions): source of the Pauli-basis lists
+  const double2* S64;  // the same in FP64 (the fused product; FP64 jobs build their Pauli-basis lists from it)
   int tiles;           // tile items of this block (tile jobs)
   int tile_prefix;     // tiles of the job's earlier blocks: the wait target
 };
@@ -84,7 +84,7 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Width-2 products of tile items in the Pauli basis. Every block is a
+// Width-2 products of FP64 tile items in the Pauli basis. Every block is a
 // Kraus map, so its superoperator S preserves Hermiticity, and in the basis
 // of Pauli products (T: per qubit, the entries (r, c) = 00, 10, 01, 11 of
 // its 2 x 2 block become I = a00 + a11, X = a01 + a10, Y = i (a01 - a10),
@@ -104,11 +104,6 @@ constexpr double kPauliZeroRel = 7.105427357601002e-15;  // 2^-47
 
 template <typename T2>
 struct Sc;
-template <>
-struct Sc<float2> {
-  using T = float;
-  __device__ __forceinline__ static float2 mk(float a, float b) { return make_float2(a, b); }
-};
 template <>
 struct Sc<double2> {
   using T = double;
@@ -193,13 +188,12 @@ __host__ __device__ __forceinline__ double pauli_entry(const double2* S, int sa,
     }
   return acc * (1.0 / 16.0);
 }
-// Whether a width-2 tile-item block takes the Pauli row lists: FP64 when they
-// cost fewer FP64 operations per group (2 per nonzero + 128 adds against 4
-// per nonzero of S's row lists); split (dense S otherwise) when R' has at
-// most half its entries.
-__host__ __device__ __forceinline__ bool pauli_better(int prec, int nnzS, int nnzR) {
-  return prec == 0 ? (2 * nnzR + 128 < 4 * nnzS) : (nnzR <= 128);
-}
+// Whether an FP64 width-2 tile-item block takes the Pauli row lists: when
+// they cost fewer FP64 operations per group (2 per nonzero + 128 adds against
+// 4 per nonzero of S's row lists). Split blocks keep the dense product: their
+// tile items are HBM-bound, and building R' (FP64, at staging) cost more than
+// it saved (1024-circuit sweep: 4,584 against 8,311 circuits/s).
+__host__ __device__ __forceinline__ bool pauli_better(int nnzS, int nnzR) { return 2 * nnzR + 128 < 4 * nnzS; }
 
 // One canonical group of a width-K split block on the shared-memory copy of
 // rho (resident items): gather its 4^K entries, multiply by S (shared
@@ -421,60 +415,6 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
   }
 }
 
-// The same tile walk for a width-2 block in the Pauli basis: the entries
-// are transformed in registers, parked in this thread's shared-memory column
-// col[slot * kThreads] for the row-list products (real R' values in val),
-// transformed back and stored.
-__device__ __forceinline__ void apply_tile16_pauli(float2* rho, unsigned long long u, const ApplyParams& p,
-                                                   const float* val, const RowLists& rl, const Tile16& t,
-                                                   float2* col) {
-  constexpr int D = 16;
-  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-  const int i = (lane % 8) + 8 * (w % 2), j = (lane / 8) + 4 * (w / 2);
-  bool diag = false;
-  const unsigned long long tt = canonical_group(u, 32, &diag);
-  if (diag && i > j) return;
-  const bool self = diag && i == j;
-  const unsigned rbase = (unsigned)deposit_zeros((tt & 0xffffffffull) * 16, t.qs, 2) + t.dep16[i];
-  const unsigned cbase = (unsigned)deposit_zeros((tt >> 32) * 16, t.qs, 2) + t.dep16[j];
-  float2 x[D];
-#pragma unroll
-  for (int l = 0; l < D; ++l) {
-    const unsigned r = rbase + t.rt[l], c = cbase + t.ct[l];
-    const bool up = r <= c;
-    float2 v = __ldcg(&rho[up ? ((unsigned long long)r | ((unsigned long long)c << p.n))
-                              : ((unsigned long long)c | ((unsigned long long)r << p.n))]);
-    if (!up) v.y = -v.y;
-    x[l] = v;
-  }
-  pauli_fwd(x);
-#pragma unroll
-  for (int a = 0; a < D; ++a) col[a * kThreads] = x[a];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int k = rl.rowptr[a]; k < rl.rowptr[a + 1]; ++k) {
-      const float v = val[k];
-      const float2 xc = col[rl.col[k] * kThreads];
-      acc.x = fmaf(v, xc.x, acc.x);
-      acc.y = fmaf(v, xc.y, acc.y);
-    }
-    x[a] = acc;
-  }
-  pauli_inv(x);
-#pragma unroll
-  for (int o = 0; o < D; ++o) {
-    float2 acc = x[o];
-    const unsigned r = rbase + t.rt[o], c = cbase + t.ct[o];
-    if (r <= c) {
-      rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
-    } else if (!self) {
-      acc.y = -acc.y;
-      rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
-    }
-  }
-}
-
 // FP64 tile items of a width-2 block in the Pauli basis: the group's entries
 // gathered into this thread's shared-memory column (as the row-list path
 // does), transformed there, multiplied by the real R' row lists into
@@ -609,7 +549,7 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
   }
   if (threadIdx.x == 0) ps->on = 0;
   __syncthreads();
-  if (!allow_pauli || s_blk->p.width != 2) return;
+  if (!allow_pauli || sizeof(T2) == 8 || s_blk->p.width != 2) return;
   // tile items of width-2 blocks: R' in FP64, structural zeros dropped, and
   // the Pauli row lists replace S's when they cost less (pauli_better)
   ps->R[threadIdx.x] = pauli_entry(s_blk->S64, threadIdx.x / 16, threadIdx.x % 16);
@@ -631,8 +571,7 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
   if (threadIdx.x == 0) {
     int nnzR = 0;
     for (int i = 0; i < 16; ++i) nnzR += __popc(ps->mask[i]);
-    const int nnzS = sizeof(T2) == 16 ? rl->rowptr[16] : 256;
-    ps->on = pauli_better(sizeof(T2) == 16 ? 0 : 1, nnzS, nnzR) ? 1 : 0;
+    ps->on = pauli_better(rl->rowptr[16], nnzR) ? 1 : 0;
     if (ps->on) {
       rl->rowptr[0] = 0;
       for (int i = 0; i < 16; ++i) rl->rowptr[i + 1] = rl->rowptr[i] + __popc(ps->mask[i]);
@@ -643,11 +582,7 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
     int k = rl->rowptr[threadIdx.x];
     for (int j = 0; j < 16; ++j)
       if ((ps->mask[threadIdx.x] >> j) & 1u) {
-        const double v = ps->R[threadIdx.x * 16 + j];
-        if (sizeof(T2) == 16)
-          reinterpret_cast<double*>(sS)[k] = v;
-        else
-          reinterpret_cast<float*>(sS)[k] = (float)v;
+        reinterpret_cast<double*>(sS)[k] = ps->R[threadIdx.x * 16 + j];
         rl->col[k] = (unsigned char)j;
         ++k;
       }
@@ -755,12 +690,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         const unsigned long long u0 = (unsigned long long)it.tile0 * upt;
         const unsigned long long u1 = min(total, u0 + (unsigned long long)it.ntiles * upt);
         for (unsigned long long u = u0; u < u1; ++u) {
-          // the resident buffer is free in tile items: one column per thread
-          float2* col = reinterpret_cast<float2*>(sR) + threadIdx.x;
           if (p.width == 1)
             apply_tile16<1>(rho, u, p, sS, s_t16);
-          else if (s_ps.on)
-            apply_tile16_pauli(rho, u, p, reinterpret_cast<const float*>(sS), s_rl, s_t16, col);
           else
             apply_tile16<2>(rho, u, p, sS, s_t16);
         }

@@ -87,7 +87,19 @@ struct SparseWork {
 __host__ __device__ __forceinline__ unsigned long long canonical_group(unsigned long long t, int rest_bits,
                                                                        bool* self) {
   // FP32 estimate (off by at most one for t < 2^31), corrected exactly in
-  // integers; the FP64 pipe stays free for the apply arithmetic.
+  // integers; the FP64 pipe stays free for the apply arithmetic. Below 2^30
+  // (every register up to 16 qubits) the conversions and the correction are
+  // 32-bit: 64-bit integer <-> float conversions run on the FP64 pipe.
+  if (t < (1ull << 30)) {
+    const unsigned int t32 = (unsigned int)t;
+    const float est = (sqrtf(8.0f * (float)t32 + 1.0f) - 1.0f) * 0.5f;
+    unsigned int b = est > 0.0f ? (unsigned int)est : 0u;  // b < 46341: (b + 1) (b + 2) < 2^31
+    while (b * (b + 1) / 2 > t32) --b;
+    while ((b + 1) * (b + 2) / 2 <= t32) ++b;
+    const unsigned int a = t32 - b * (b + 1) / 2;
+    *self = a == b;
+    return (unsigned long long)a | ((unsigned long long)b << rest_bits);
+  }
   const float est = (sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f;
   unsigned long long b = est > 0.0f ? (unsigned long long)est : 0ull;
   while (b * (b + 1) / 2 > t) --b;

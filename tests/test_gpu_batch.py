@@ -104,9 +104,9 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
     """Flops and HBM bytes tq_batch_work must report for one job, from the
     plan's blocks: every job runs its canonical groups (Hermitian mode);
     FP64 counts nonzeros (a diagonal block has D of them), split counts all;
-    width-2 blocks of tile jobs that the kernel runs in the Pauli basis count
-    4 per nonzero of R' plus 128 (FP64 when that is cheaper than 4 per
-    nonzero of S, split when R' has at most 128 nonzeros)."""
+    FP64 width-2 blocks of tile jobs that the kernel runs in the Pauli basis
+    (when that is cheaper than 4 per nonzero of S) count 4 per nonzero of R'
+    plus 128."""
     esz = 16 if precision == "fp64" else 8
     resident = esz * 4 ** n <= 64 * 1024
     herm = True
@@ -116,9 +116,9 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
         groups = M * (M + 1) // 2 if herm else 4 ** (n - w)
         nnz = 4 ** w if (precision == "fp64" and diagonal_fp64) else 16 ** w
         per = 8 * nnz
-        if not resident and w == 2:
+        if precision == "fp64" and not resident and w == 2:
             nr = _pauli_nonzeros(S)
-            if (2 * nr + 128 < 4 * nnz) if precision == "fp64" else (nr <= 128):
+            if 2 * nr + 128 < 4 * nnz:
                 per = 4 * nr + 128
         flops += per * groups
         if not resident:
@@ -184,9 +184,16 @@ def test_batch_job_alone_equals_in_mix_and_single_state(tq):
         alone.wait()
         assert np.array_equal(alone.rho(0), mix.rho(j))          # bitwise: same kernels, same order
         assert np.array_equal(alone.result(0), mix.result(j))
-        with tq.State(n, "fp64", engine="dfma") as st:    # both compute the canonical groups, same DFMA arithmetic
+        with tq.State(n, "fp64", engine="dfma") as st:
             st.run(ops, width=2)
-            assert np.array_equal(st.rho(), mix.rho(j))
+            if 16 * 4 ** n <= 64 * 1024:
+                # resident jobs: both compute the canonical groups with the
+                # same DFMA arithmetic in the same order
+                assert np.array_equal(st.rho(), mix.rho(j))
+            else:
+                # tile jobs may run width-2 blocks in the Pauli basis (other
+                # rounding): both FP64, each within 1e-12 of the other
+                assert np.max(np.abs(st.rho() - mix.rho(j))) < TOL64
         alone.free()
     mix.free()
 

@@ -1,6 +1,7 @@
 """Serving loop (tq_server): continuous batching of circuit requests. Each
-request's result must be the same alone and in the mix (FP64: bitwise; the
-arithmetic per group is identical), admission must respect the HBM budget,
+request's result must match the single-state path (FP64: bitwise for
+requests resident in shared memory, whose arithmetic per group is identical; within
+1e-12 for the others), admission must respect the HBM budget,
 and results must match the oracle."""
 import numpy as np
 import pytest
@@ -67,7 +68,10 @@ def test_served_results_same_alone_and_in_mix(tq, precision):
             for i, m in enumerate(masks):
                 assert abs(got[2 + i] - O.expect_z(want, m)) < SPLIT_Z, (k, i)
         else:
-            assert np.array_equal(got, alone), k
+            if 16 * 4 ** n <= 64 * 1024:
+                assert np.array_equal(got, alone), k    # resident: the same DFMA arithmetic, same order
+            else:
+                assert np.max(np.abs(got - alone)) < TOL64, k   # tile jobs: width-2 blocks may run in the Pauli basis
             assert abs(got[0] - O.trace(want).real) < TOL64
             for i, m in enumerate(masks):
                 assert abs(got[2 + i] - O.expect_z(want, m)) < TOL64

@@ -1,8 +1,9 @@
 """CPU pins of the arithmetic of the FP64-accurate tensor-core pass
 (csrc/tq_apply_oz.cu), emulated bit by bit in numpy: every FP64 operand's
 significand aligned to the largest exponent of its group (inputs) or row
-(superoperator), rounded to nearest (54 bits), cut into seven balanced 8-bit
-digits (the bytes of F + 0x0080808080808080, minus 128), the digit products
+(superoperator), at least 64, rounded to nearest (54 bits), cut into seven
+balanced 8-bit digits (the bytes of F + 0x0080808080808080, minus 128, signed
+by one FP16 multiply-add), the digit products
 summed exactly per order t = i + j (orders 0..7, each in its own FP32
 accumulator), each accumulator turned into its integer by the 1.5 * 2^23
 float addition (orders 6 and 7 rounded to units of 2^8 and 2^16), the
@@ -25,41 +26,45 @@ def fields(v: float):
 
 
 def aligned_offset(v: float, E: int) -> int:
-    """F + 0x0080808080808080: v's significand aligned to biased exponent E
-    and rounded to nearest (ties away from zero), F < 2^54."""
+    """F + 0x0080808080808080 the kernel's way: M2 = the significand (implicit
+    bit set) times 4, T = M2 >> (E - e_v) (0 for shifts of 64 or more),
+    (T + 0x0101010101010101) >> 1."""
     _, ev, frac = fields(v)
     sh = E - ev
-    M1 = ((1 << 52) | frac) << 1
-    if ev == 0 or sh > 54:
-        F = 0
-    elif sh == 0:
-        F = M1
-    else:
-        F = ((M1 >> (sh - 1)) + 1) >> 1
-    assert F < (1 << 54)
-    return F + OFFSET
+    M2 = ((1 << 52) | frac) << 2
+    T = M2 >> sh if sh < 64 else 0
+    out = (T + 0x0101010101010101) >> 1
+    # the same as v's significand (times 2: 54 bits) aligned to E and
+    # rounded to nearest, ties away from zero (zeros and subnormals: 0), plus
+    # the offset
+    M1 = 0 if ev == 0 else ((1 << 52) | frac) << 1
+    F = int(Fraction(M1, 2 ** sh) + Fraction(1, 2)) if M1 else 0
+    assert out == F + OFFSET and F < (1 << 54)
+    return out
 
 
-def fp16_digit(byte: int) -> float:
+def fp16_digit(byte: int, neg: bool) -> float:
     """The kernel's FP16 arithmetic on one half: the byte placed in the low
-    mantissa byte of FP16 1024, minus 1152 (both steps exact in FP16)."""
+    mantissa byte of FP16 1024, times s = -1 or +1, plus -1152 s (one
+    multiply-add; every intermediate is exact in FP16)."""
     w = np.array([0x6400 | byte], dtype=np.uint16).view(np.float16)[0]
-    d = np.float16(w - np.float16(1152.0))
-    assert float(d) == byte - 128
+    s = np.float16(-1.0 if neg else 1.0)
+    d = np.float16(np.float32(w) * np.float32(s) + np.float32(-1152.0) * np.float32(s))
+    assert float(d) == (byte - 128) * (-1 if neg else 1)
     return float(d)
 
 
 def digits7(v: float, E: int):
-    """The seven digits of v (sign applied): integers in [-128, 128)."""
+    """The seven digits of v (sign applied): integers in [-128, 128]."""
     sgn = fields(v)[0]
     Fp = aligned_offset(v, E)
     assert Fp >> 56 == 0                                   # the offset never carries out of byte 6
-    d = [fp16_digit((Fp >> (8 * (6 - i))) & 0xFF) for i in range(7)]
-    return [-x if sgn else x for x in d]
+    return [fp16_digit((Fp >> (8 * (6 - i))) & 0xFF, bool(sgn)) for i in range(7)]
 
 
 def max_exp(vals):
-    return max(fields(float(v))[1] for v in vals)
+    """The alignment exponent: the largest biased exponent, at least 64."""
+    return max(64, max(fields(float(v))[1] for v in vals))
 
 
 def magic_bits(u):
@@ -168,6 +173,17 @@ def test_recombined_dot_products_are_fp64_accurate():
     # the rounding of orders 6 and 7 and one final rounding: below 2^-51 of
     # the product of the alignments (measured: ~2 x 2^-53)
     assert worst < 2.0 ** -51, worst / 2.0 ** -53
+
+
+def test_tiny_groups_are_aligned_to_the_floor_exponent():
+    # a group whose largest entry is below 2^-959 is aligned to 2^-959: the
+    # result stays within 2^-51 of that alignment times the row's
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(32) * 1e-300
+    r = rng.standard_normal(32)
+    y, E, G = oz_dot(x, r)
+    assert E == 64
+    assert abs(Fraction(y) - exact_dot(x, r)) < Fraction(align(E) * align(G)) * Fraction(1, 2 ** 51)
 
 
 def test_zero_rows_and_groups_give_exact_zeros():
