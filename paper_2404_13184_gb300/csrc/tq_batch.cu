@@ -33,6 +33,8 @@ struct tq_batch {
   int never_ready_job = -1;       // test hook
   // device
   DevBuf arena, blob, sops, sb64, sb32, djobs, dblks, ditems, counters, ctl, results;
+  DevBuf pauli, pwork;  // Pauli-basis records of width-2 tile-job blocks and their sb64 offsets
+  int n_pauli = 0;
   PinBuf host_out;  // results + error flag
   size_t n_items = 0;
   size_t arena_bytes = 0;
@@ -72,9 +74,8 @@ int default_tile_log2(int n, int prec) {
 
 // Algorithmic flops and HBM bytes of one run (see tq_batch_work): one CTA
 // per job, threads over its blocks; FP64 counts the nonzeros of S by their
-// bit patterns, as the row-list staging does, and FP64 width-2 blocks of
-// tile jobs make the kernel's Pauli-basis choice (pauli_better on the same
-// R').
+// bit patterns, as the row-list staging does; width-2 blocks of tile jobs
+// whose Pauli-basis record is taken count the Pauli-basis product.
 __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restrict__ blks, int prec,
                              unsigned long long* __restrict__ out) {
   const BJob& jb = jobs[blockIdx.x];
@@ -92,19 +93,10 @@ __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restri
     }
     // flops per group: 8 per complex multiply-add of S (its nonzeros, or all
     // of them), or in the Pauli basis 4 per real-times-complex multiply-add
-    // plus the 128 adds of the two basis changes
+    // (FP64: the nonzeros of R'; split: all 256) plus the 128 adds of the two
+    // basis changes
     unsigned long long per = 8ull * nnz;
-    if (prec == 0 && !jb.resident && bk.p.width == 2) {
-      double Rp[256], mx = 0.0;
-      for (int e = 0; e < 256; ++e) {
-        Rp[e] = pauli_entry(bk.S64, e / 16, e % 16);
-        mx = fmax(mx, fabs(Rp[e]));
-      }
-      const double thr = mx * kPauliZeroRel;
-      int nnzR = 0;
-      for (int e = 0; e < 256; ++e) nnzR += fabs(Rp[e]) > thr;
-      if (pauli_better((int)nnz, nnzR)) per = 4ull * nnzR + 128;
-    }
+    if (bk.pauli && bk.pauli->on) per = 4ull * (prec == 0 ? (unsigned long long)bk.pauli->nnz : 256ull) + 128;
     const unsigned long long groups = jb.herm ? bk.p.n_canon : bk.p.n_groups;
     fl += per * groups;
     if (!jb.resident) by += (jb.herm ? N + R : 2 * N) * esz;
@@ -128,6 +120,8 @@ tq_status finalize(tq_batch* b) {
   HostTables all;
   std::vector<BJob> hjobs(b->jobs.size());
   std::vector<BBlk> hblks;
+  std::vector<long long> blk_rec;          // per block: its Pauli record, or -1
+  std::vector<unsigned long long> rec_sb;  // per record: its block's sb64 offset
   size_t arena = 0;
   b->rho_off.assign(b->jobs.size(), 0);
   int max_dim2 = 1;
@@ -177,6 +171,12 @@ tq_status finalize(tq_batch* b) {
       std::memset(&bb, 0, sizeof(bb));
       bb.p = J.prog.params[k];
       bb.S = reinterpret_cast<const void*>(J.prog.sb_off[k] + sbb);  // offset; made absolute below
+      if (!hj.resident && bb.p.width == 2) {
+        blk_rec.push_back((long long)rec_sb.size());
+        rec_sb.push_back((unsigned long long)(J.prog.sb_off[k] + sbb));
+      } else {
+        blk_rec.push_back(-1);
+      }
       hblks.push_back(bb);
     }
     if (set_tiles(hblks.data() + hj.block0, hj.n_blocks, hj.tile_log2, hj.herm != 0, tiled16_job(J.n, b->prec)) >= (1ll << 31))
@@ -228,6 +228,9 @@ tq_status finalize(tq_batch* b) {
   if (e == cudaSuccess) e = alloc(b->counters, hjobs.size() * sizeof(int));
   if (e == cudaSuccess) e = alloc(b->ctl, 256);
   if (e == cudaSuccess) e = alloc(b->results, hjobs.size() * kResults * sizeof(double));
+  b->n_pauli = (int)rec_sb.size();
+  if (e == cudaSuccess) e = alloc(b->pauli, std::max<size_t>(1, rec_sb.size()) * sizeof(PauliRec));
+  if (e == cudaSuccess) e = alloc(b->pwork, std::max<size_t>(1, rec_sb.size()) * sizeof(unsigned long long));
   if (e != cudaSuccess) return to_status(e);
   if (b->host_out.cap < hjobs.size() * kResults * sizeof(double) + 64) {
     if (b->host_out.ptr) cudaFreeHost(b->host_out.ptr);
@@ -239,10 +242,10 @@ tq_status finalize(tq_batch* b) {
   {
     const size_t esz = b->prec == TQ_FP64 ? sizeof(double2) : sizeof(float2);
     char* sbase = static_cast<char*>(b->prec == TQ_FP64 ? b->sb64.ptr : b->sb32.ptr);
-    for (BBlk& bb : hblks) {
-      const size_t off = reinterpret_cast<size_t>(bb.S);
-      bb.S = sbase + off * esz;
-      bb.S64 = static_cast<const double2*>(b->sb64.ptr) + off;
+    for (size_t k = 0; k < hblks.size(); ++k) {
+      BBlk& bb = hblks[k];
+      bb.S = sbase + reinterpret_cast<size_t>(bb.S) * esz;
+      bb.pauli = blk_rec[k] < 0 ? nullptr : static_cast<const PauliRec*>(b->pauli.ptr) + blk_rec[k];
     }
   }
   e = cudaMemcpy(b->blob.ptr, h.data(), P.blob_bytes, cudaMemcpyHostToDevice);
@@ -251,6 +254,8 @@ tq_status finalize(tq_batch* b) {
     e = cudaMemcpy(b->dblks.ptr, hblks.data(), hblks.size() * sizeof(BBlk), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !items.empty())
     e = cudaMemcpy(b->ditems.ptr, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !rec_sb.empty())
+    e = cudaMemcpy(b->pwork.ptr, rec_sb.data(), rec_sb.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return to_status(e);
 
   const size_t smem = b->prec == TQ_FP64 ? apply_smem<double2>() : apply_smem<float2>();
@@ -285,6 +290,8 @@ tq_status finalize(tq_batch* b) {
                 reinterpret_cast<const FuseWork*>(d + P.o_work), (int)all.work.size(),
                 static_cast<double2*>(b->sb64.ptr),
                 b->prec == TQ_SPLIT ? static_cast<float2*>(b->sb32.ptr) : nullptr, st);
+    launch_pauli_lists(static_cast<const double2*>(b->sb64.ptr), static_cast<const unsigned long long*>(b->pwork.ptr),
+                       b->n_pauli, b->prec == TQ_FP64 ? 0 : 1, static_cast<PauliRec*>(b->pauli.ptr), st);
   }
   cudaMemsetAsync(b->counters.ptr, 0, n_jobs * sizeof(int), st);
   cudaMemsetAsync(b->ctl.ptr, 0, 256, st);
@@ -467,7 +474,7 @@ void tq_batch_free(tq_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
-  for (DevBuf* d : {&b->arena, &b->blob, &b->sops, &b->sb64, &b->sb32, &b->djobs, &b->dblks, &b->ditems,
+  for (DevBuf* d : {&b->arena, &b->blob, &b->sops, &b->sb64, &b->sb32, &b->djobs, &b->dblks, &b->ditems, &b->pauli, &b->pwork,
                     &b->counters, &b->ctl, &b->results})
     if (d->ptr) cudaFree(d->ptr);
   if (b->host_out.ptr) cudaFreeHost(b->host_out.ptr);

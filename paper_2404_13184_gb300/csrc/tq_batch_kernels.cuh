@@ -38,12 +38,26 @@ struct BJob {
   unsigned long long masks[kMaxMasks];
 };
 
+// Pauli-basis row lists of one width-2 block of a tile job (see the Pauli
+// section below), built once per run by k_pauli_lists and copied by every
+// tile item of the block when it stages the block.
+struct PauliRec {
+  int on;                     // the block's tile items take these lists
+  int nnz;                    // nonzeros of R' kept
+  unsigned short rowptr[17];  // row r's nonzeros: rowptr[r] .. rowptr[r + 1] - 1
+  unsigned short pad_;
+  unsigned char col[256];
+  double val[256];            // FP64 jobs: the row lists' values; split jobs: R' as 256 floats,
+                              // dense and transposed (entry (a, b) at b * 16 + a)
+};
+static_assert(sizeof(PauliRec) == 2352, "record layout");
+
 struct BBlk {
   ApplyParams p;
-  const void* S;       // fused superoperator, 4^w x 4^w row-major (double2 or float2)
-  const double2* S64;  // the same in FP64 (the fused product; FP64 jobs build their Pauli-basis lists from it)
-  int tiles;           // tile items of this block (tile jobs)
-  int tile_prefix;     // tiles of the job's earlier blocks: the wait target
+  const void* S;            // fused superoperator, 4^w x 4^w row-major (double2 or float2)
+  const PauliRec* pauli;    // width-2 blocks of tile jobs: their Pauli-basis lists; else null
+  int tiles;                // tile items of this block (tile jobs)
+  int tile_prefix;          // tiles of the job's earlier blocks: the wait target
 };
 
 struct BItem {
@@ -52,6 +66,12 @@ struct BItem {
   int tile0;   // tile item: first tile; resident item: first block
   int ntiles;  // tile item: tiles; resident item: blocks
 };
+
+// -v by its sign bit: an integer operation, off the FP64 pipe that bounds
+// the FP64 paths
+__device__ __forceinline__ double flip_sign(double v) {
+  return __hiloint2double(__double2hiint(v) ^ (int)0x80000000, __double2loint(v));
+}
 
 template <typename T2>
 struct Cx;
@@ -84,7 +104,7 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Width-2 products of FP64 tile items in the Pauli basis. Every block is a
+// Width-2 products of tile items in the Pauli basis. Every block is a
 // Kraus map, so its superoperator S preserves Hermiticity, and in the basis
 // of Pauli products (T: per qubit, the entries (r, c) = 00, 10, 01, 11 of
 // its 2 x 2 block become I = a00 + a11, X = a01 + a10, Y = i (a01 - a10),
@@ -104,6 +124,11 @@ constexpr double kPauliZeroRel = 7.105427357601002e-15;  // 2^-47
 
 template <typename T2>
 struct Sc;
+template <>
+struct Sc<float2> {
+  using T = float;
+  __device__ __forceinline__ static float2 mk(float a, float b) { return make_float2(a, b); }
+};
 template <>
 struct Sc<double2> {
   using T = double;
@@ -175,25 +200,104 @@ __host__ __device__ __forceinline__ void pauli_row(int slot, int l[4], int cre[4
       cim[2 * u + v] = fre[0][u] * fim[1][v] + fim[0][u] * fre[1][v];
     }
 }
-__host__ __device__ __forceinline__ double pauli_entry(const double2* S, int sa, int sb) {
-  int la[4], lb[4], ar[4], ai[4], br[4], bi[4];
-  pauli_row(sa, la, ar, ai);
-  pauli_row(sb, lb, br, bi);
-  double acc = 0.0;
-  for (int u = 0; u < 4; ++u)
-    for (int v = 0; v < 4; ++v) {
-      const double2 sv = S[la[u] * 16 + lb[v]];
-      const double tr = ar[u] * sv.x - ai[u] * sv.y, ti = ar[u] * sv.y + ai[u] * sv.x;  // T[sa][l] S[l][m]
-      acc += tr * br[v] + ti * bi[v];                                                // Re (t conj(T[sb][m]))
-    }
-  return acc * (1.0 / 16.0);
+// Whether a width-2 tile-item block takes the Pauli basis. FP64: when its
+// row lists cost fewer FP64 operations per group (2 per nonzero + 128 adds
+// against 4 per nonzero of S's row lists). Split: always; it runs R' as a
+// dense real 16 x 16 product (512 FFMA + 128 adds per group against 1,024
+// FFMA for the complex S), unrolled like the dense split product (the
+// row-list loop, a chain of dependent shared-memory loads per nonzero, was
+// latency-bound there: 1024-circuit sweep 6,971 against 8,440 circuits/s
+// for the dense complex product).
+__host__ __device__ __forceinline__ bool pauli_better(int prec, int nnzS, int nnzR) {
+  return prec == 0 ? 2 * nnzR + 128 < 4 * nnzS : true;
 }
-// Whether an FP64 width-2 tile-item block takes the Pauli row lists: when
-// they cost fewer FP64 operations per group (2 per nonzero + 128 adds against
-// 4 per nonzero of S's row lists). Split blocks keep the dense product: their
-// tile items are HBM-bound, and building R' (FP64, at staging) cost more than
-// it saved (1024-circuit sweep: 4,584 against 8,311 circuits/s).
-__host__ __device__ __forceinline__ bool pauli_better(int nnzS, int nnzR) { return 2 * nnzR + 128 < 4 * nnzS; }
+
+// One CTA of 256 threads per record: R' = T S T^dagger / 16 of the block's
+// FP64 fused superoperator in two passes of additions only (T's entries are
+// +-1 and +-i): U = T S (thread (a, m)), then R'[a][b] = Re sum_m U[a][m]
+// conj(T[b][m]) / 16 (thread (a, b)). Entries at most 2^-47 of the largest
+// are dropped; the remaining ones form the row lists (FP64 jobs) or the
+// dense transposed R' rounded to FP32 (split jobs), taken when pauli_better
+// says so. S's
+// nonzeros are counted by bit pattern, as the FP64 staging does.
+static __global__ void __launch_bounds__(256) k_pauli_lists(const double2* __restrict__ sb64,
+                                                            const unsigned long long* __restrict__ sb_off, int prec,
+                                                            PauliRec* __restrict__ out) {
+  __shared__ double2 U[256];
+  __shared__ double red[8];
+  __shared__ unsigned int rowmask[16];
+  const int t = threadIdx.x, a = t >> 4, mb = t & 15;
+  const double2* S = sb64 + sb_off[blockIdx.x];
+  PauliRec& rec = out[blockIdx.x];
+  const double2 st = S[t];
+  const int nnzS = __syncthreads_count(((__double_as_longlong(st.x) | __double_as_longlong(st.y)) << 1) != 0);
+  int l[4], cre[4], cim[4];
+  pauli_row(a, l, cre, cim);
+  double ur = 0.0, ui = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    // (cre + i cim)(s.x + i s.y), one of cre, cim zero and the other +-1
+    const double2 sv = S[l[u] * 16 + mb];
+    const double dx = cim[u] == 0 ? sv.x : sv.y, dy = cim[u] == 0 ? sv.y : sv.x;
+    const int sx = cim[u] == 0 ? cre[u] : -cim[u], sy = cim[u] == 0 ? cre[u] : cim[u];
+    ur = sx > 0 ? ur + dx : ur - dx;
+    ui = sy > 0 ? ui + dy : ui - dy;
+  }
+  U[t] = make_double2(ur, ui);
+  __syncthreads();
+  pauli_row(mb, l, cre, cim);  // row b = mb of T
+  double r = 0.0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    // Re (U[a][m] conj(cre + i cim)) = U.x cre + U.y cim
+    const double2 uv = U[a * 16 + l[v]];
+    const double d = cim[v] == 0 ? uv.x : uv.y;
+    const int sg = cim[v] == 0 ? cre[v] : cim[v];
+    r = sg > 0 ? r + d : r - d;
+  }
+  r *= 0.0625;
+  double mx = fabs(r);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+  for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
+  const bool keep = fabs(r) > mx * kPauliZeroRel;
+  const unsigned int ball = __ballot_sync(0xffffffffu, keep);
+  if ((t & 15) == 0) rowmask[a] = (ball >> (t & 16)) & 0xffffu;
+  __syncthreads();
+  int off = 0, nnz = 0;
+  for (int i = 0; i < 16; ++i) {
+    const int c = __popc(rowmask[i]);
+    off += i < a ? c : 0;
+    nnz += c;
+  }
+  if (prec == 0) {
+    if (keep) {
+      const int k = off + __popc(rowmask[a] & ((1u << mb) - 1u));
+      rec.col[k] = (unsigned char)mb;
+      rec.val[k] = r;
+    }
+  } else {
+    reinterpret_cast<float*>(rec.val)[mb * 16 + a] = keep ? (float)r : 0.f;  // dense, transposed
+  }
+  if (t <= 16) {
+    int o = 0;
+    for (int i = 0; i < t; ++i) o += __popc(rowmask[i]);
+    rec.rowptr[t] = (unsigned short)o;
+  }
+  if (t == 0) {
+    rec.nnz = nnz;
+    rec.on = pauli_better(prec, nnzS, nnz) ? 1 : 0;
+  }
+}
+
+inline cudaError_t launch_pauli_lists(const double2* sb64, const unsigned long long* sb_off, int n_rec, int prec,
+                                      PauliRec* out, cudaStream_t st) {
+  if (n_rec <= 0) return cudaSuccess;
+  k_pauli_lists<<<n_rec, 256, 0, st>>>(sb64, sb_off, prec, out);
+  return cudaGetLastError();
+}
 
 // One canonical group of a width-K split block on the shared-memory copy of
 // rho (resident items): gather its 4^K entries, multiply by S (shared
@@ -247,6 +351,7 @@ __device__ __forceinline__ void apply_group(T2* rho, unsigned long long t, const
 // result is that of the dense product (an FMA with a zero product is exact).
 struct RowLists {
   int rowptr[17];
+  unsigned int mask[16];  // staging: nonzero columns of each row
   unsigned char col[kSEntries];
 };
 static_assert(16 * kThreads * 16 <= kResidentBytes, "operand columns of a width-2 FP64 tile item");
@@ -301,7 +406,7 @@ __device__ __forceinline__ void apply_group_lists_global(double2* rho, unsigned 
       e = base + p.off[l];
     }
     double2 v = __ldcg(&rho[e]);
-    if (conj) v.y = -v.y;
+    if (conj) v.y = flip_sign(v.y);
     mine[l * kThreads] = v;
   }
 #pragma unroll
@@ -313,7 +418,7 @@ __device__ __forceinline__ void apply_group_lists_global(double2* rho, unsigned 
       if (r <= c) {
         rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
       } else if (!self) {
-        acc.y = -acc.y;
+        acc.y = flip_sign(acc.y);
         rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
       }
     } else {
@@ -349,7 +454,7 @@ __device__ __forceinline__ void apply_group_lists_resident(double2* sR, unsigned
       if (HERM) {
         const unsigned int r = rb + (off & rmask), c = cb + (off >> p.n);
         v = sR[r <= c ? (r | (c << p.n)) : (c | (r << p.n))];
-        if (r > c) v.y = -v.y;
+        if (r > c) v.y = flip_sign(v.y);
       } else {
         v = sR[base + off];
       }
@@ -366,7 +471,7 @@ __device__ __forceinline__ void apply_group_lists_resident(double2* sR, unsigned
       if (r <= c) {
         sR[r | (c << p.n)] = acc;
       } else if (!self) {
-        acc.y = -acc.y;
+        acc.y = flip_sign(acc.y);
         sR[c | (r << p.n)] = acc;
       }
     } else {
@@ -415,6 +520,95 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
   }
 }
 
+// The same tile walk for a width-2 block in the Pauli basis, over tiles u0 ..
+// u1 - 1: a group's entries are transformed in registers, multiplied by R'
+// (dense real 16 x 16, stored transposed in shared memory so that column b
+// is one run of 16 floats read by warp-uniform broadcast), transformed back
+// and stored. The product runs column by column, and each column's register
+// pair, once consumed, receives the next tile's entry of the same index: the
+// next tile's loads are in flight during this tile's 512 FFMA. Tiles hold
+// disjoint canonical groups, so no load of tile u + 1 sees a store of tile u.
+__device__ __forceinline__ void apply_tiles16_pauli(float2* rho, unsigned long long u0, unsigned long long u1,
+                                                    const ApplyParams& p, const float* Rt, const Tile16& t) {
+  constexpr int D = 16;
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int i = (lane % 8) + 8 * (w % 2), j = (lane / 8) + 4 * (w / 2);
+  // this thread's group in tile u: row / column bases; canonical (active);
+  // self-conjugate
+  auto group = [&](unsigned long long u, unsigned& rb, unsigned& cb, bool& act, bool& self) {
+    bool diag = false;
+    const unsigned long long tt = canonical_group(u, 32, &diag);
+    act = !(diag && i > j);
+    self = diag && i == j;
+    rb = (unsigned)deposit_zeros((tt & 0xffffffffull) * 16, t.qs, 2) + t.dep16[i];
+    cb = (unsigned)deposit_zeros((tt >> 32) * 16, t.qs, 2) + t.dep16[j];
+  };
+  // stored location of entry l (upper triangle; up: read as is)
+  auto where = [&](unsigned rb, unsigned cb, int l, bool& up) {
+    const unsigned r = rb + t.rt[l], c = cb + t.ct[l];
+    up = r <= c;
+    return up ? ((unsigned long long)r | ((unsigned long long)c << p.n)) : ((unsigned long long)c | ((unsigned long long)r << p.n));
+  };
+  if (u0 >= u1) return;
+  unsigned rb, cb;
+  bool act, self;
+  group(u0, rb, cb, act, self);
+  float2 x[D];
+  unsigned upm = 0;  // bit l: entry l read as is (else conjugated)
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    bool up;
+    const unsigned long long idx = where(rb, cb, l, up);
+    x[l] = act ? __ldcg(&rho[idx]) : make_float2(0.f, 0.f);
+    upm |= (up ? 1u : 0u) << l;
+  }
+  for (unsigned long long u = u0; u < u1; ++u) {
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (!((upm >> l) & 1u)) x[l].y = -x[l].y;
+    pauli_fwd(x);
+    const bool more = u + 1 < u1;
+    unsigned rbn = 0, cbn = 0, upn = 0;
+    bool actn = false, selfn = false;
+    if (more) group(u + 1, rbn, cbn, actn, selfn);
+    float2 y[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) y[a] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b2 = 0; b2 < D; ++b2) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float v = Rt[b2 * D + a];
+        y[a].x = fmaf(v, x[b2].x, y[a].x);
+        y[a].y = fmaf(v, x[b2].y, y[a].y);
+      }
+      bool up;
+      const unsigned long long idx = where(rbn, cbn, b2, up);
+      if (more && actn) x[b2] = __ldcg(&rho[idx]);
+      upn |= (up ? 1u : 0u) << b2;
+    }
+    pauli_inv(y);
+    if (act) {
+#pragma unroll
+      for (int o = 0; o < D; ++o) {
+        float2 acc = y[o];
+        const unsigned r = rb + t.rt[o], c = cb + t.ct[o];
+        if (r <= c) {
+          rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+        } else if (!self) {
+          acc.y = -acc.y;
+          rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+        }
+      }
+    }
+    rb = rbn;
+    cb = cbn;
+    act = actn;
+    self = selfn;
+    upm = upn;
+  }
+}
+
 // FP64 tile items of a width-2 block in the Pauli basis: the group's entries
 // gathered into this thread's shared-memory column (as the row-list path
 // does), transformed there, multiplied by the real R' row lists into
@@ -437,7 +631,7 @@ __device__ __forceinline__ void apply_group_pauli_global(double2* rho, unsigned 
     const bool conj = r > c;
     double2 v = __ldcg(&rho[conj ? ((unsigned long long)c | ((unsigned long long)r << p.n))
                                  : ((unsigned long long)r | ((unsigned long long)c << p.n))]);
-    if (conj) v.y = -v.y;
+    if (conj) v.y = flip_sign(v.y);
     mine[l * kThreads] = v;
   }
 #pragma unroll
@@ -473,7 +667,7 @@ __device__ __forceinline__ void apply_group_pauli_global(double2* rho, unsigned 
     if (r <= c) {
       rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
     } else if (!self) {
-      acc.y = -acc.y;
+      acc.y = flip_sign(acc.y);
       rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
     }
   }
@@ -483,27 +677,26 @@ __device__ __forceinline__ void apply_group_pauli_global(double2* rho, unsigned 
 // (split) or as row lists (FP64; zero tests on the bit patterns, so -0.0
 // counts as zero). The row lists take rows in order, each thread i < D
 // placing row i after the counts of rows < i.
-// Shared state of the Pauli-basis decision of a staged block.
-struct PauliStage {
-  double R[256];       // R' of a width-2 block, FP64
-  double thr;          // structural-zero threshold
-  unsigned short mask[16];
-  int on;              // the staged block takes the Pauli row lists
-};
-
 template <typename T2>
 __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS, RowLists* rl, Tile16* t16,
-                                            PauliStage* ps, bool allow_pauli) {
+                                            int* pauli_on, bool allow_pauli) {
   static_assert(sizeof(BBlk) % 8 == 0 && sizeof(BBlk) / 8 <= kThreads, "descriptor copied one word per thread");
   if (threadIdx.x < sizeof(BBlk) / 8)  // in parallel: one 8-byte word per thread
     reinterpret_cast<unsigned long long*>(s_blk)[threadIdx.x] = reinterpret_cast<const unsigned long long*>(blk)[threadIdx.x];
   __syncthreads();
-  const int D = 1 << (2 * s_blk->p.width);
+  const ApplyParams& p = s_blk->p;
+  const int K = p.width, D = 1 << (2 * K);
   const T2* S = static_cast<const T2*>(s_blk->S);
-  if (sizeof(T2) == 8) {
-    for (int e = threadIdx.x; e < D * D; e += blockDim.x) sS[e] = S[e];
-    const ApplyParams& p = s_blk->p;
-    const int K = p.width;
+  // tile items of width-2 blocks take the Pauli basis when the block's
+  // record says so (one word, the same for every thread)
+  const PauliRec* pr = allow_pauli ? s_blk->pauli : nullptr;
+  const bool pauli = pr != nullptr && pr->on != 0;
+  const int e = threadIdx.x;  // one superoperator entry per thread (D * D <= 256)
+  if constexpr (sizeof(T2) == 8) {
+    if (pauli)
+      reinterpret_cast<float*>(sS)[e] = reinterpret_cast<const float*>(pr->val)[e];  // R' dense, transposed
+    else if (e < D * D)
+      sS[e] = S[e];
     if (threadIdx.x < 16) {
       int qs[2] = {p.q[0], K == 2 ? p.q[1] : 0};
       if (K == 2 && qs[0] > qs[1]) {
@@ -523,70 +716,41 @@ __device__ __forceinline__ void stage_block(const BBlk* blk, BBlk* s_blk, T2* sS
         t16->ct[threadIdx.x] = ct;
       }
     }
+  } else if (pauli) {
+    // FP64 Pauli row lists as they are
+    const int nnz = pr->nnz;
+    if (e <= 16) rl->rowptr[e] = pr->rowptr[e];
+    for (int k = e; k < nnz; k += blockDim.x) {
+      rl->col[k] = pr->col[k];
+      reinterpret_cast<double*>(sS)[k] = pr->val[k];
+    }
   } else {
-    const unsigned long long* bits = reinterpret_cast<const unsigned long long*>(S);
-    unsigned int m = 0;
-    if (threadIdx.x < D)
-      for (int j = 0; j < D; ++j) {
-        const int e = threadIdx.x * D + j;
-        if (((bits[2 * e] | bits[2 * e + 1]) << 1) != 0ull) m |= 1u << j;
-      }
-    if (threadIdx.x < D) rl->rowptr[threadIdx.x + 1] = __popc(m);
-    if (threadIdx.x == 0) rl->rowptr[0] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0)
-      for (int i = 1; i <= D; ++i) rl->rowptr[i] += rl->rowptr[i - 1];
-    __syncthreads();
-    if (threadIdx.x < D) {
-      int k = rl->rowptr[threadIdx.x];
-      for (int j = 0; j < D; ++j)
-        if ((m >> j) & 1u) {
-          sS[k] = S[threadIdx.x * D + j];
-          rl->col[k] = (unsigned char)j;
-          ++k;
-        }
+    // FP64 row lists of S: nonzero by bit pattern (-0.0 counts as zero), row
+    // masks by warp ballot (a row's D entries share a warp), each kept entry
+    // placed after the nonzeros of the rows and columns before it
+    double2 v = make_double2(0.0, 0.0);
+    bool keep = false;
+    if (e < D * D) {
+      v = S[e];
+      keep = ((__double_as_longlong(v.x) | __double_as_longlong(v.y)) << 1) != 0;
     }
-  }
-  if (threadIdx.x == 0) ps->on = 0;
-  __syncthreads();
-  if (!allow_pauli || sizeof(T2) == 8 || s_blk->p.width != 2) return;
-  // tile items of width-2 blocks: R' in FP64, structural zeros dropped, and
-  // the Pauli row lists replace S's when they cost less (pauli_better)
-  ps->R[threadIdx.x] = pauli_entry(s_blk->S64, threadIdx.x / 16, threadIdx.x % 16);
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double mx = 0.0;
-    for (int e = threadIdx.x; e < 256; e += 32) mx = fmax(mx, fabs(ps->R[e]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) ps->thr = mx * kPauliZeroRel;
-  }
-  __syncthreads();
-  if (threadIdx.x < 16) {
-    unsigned m = 0;
-    for (int j = 0; j < 16; ++j)
-      if (fabs(ps->R[threadIdx.x * 16 + j]) > ps->thr) m |= 1u << j;
-    ps->mask[threadIdx.x] = (unsigned short)m;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int nnzR = 0;
-    for (int i = 0; i < 16; ++i) nnzR += __popc(ps->mask[i]);
-    ps->on = pauli_better(rl->rowptr[16], nnzR) ? 1 : 0;
-    if (ps->on) {
-      rl->rowptr[0] = 0;
-      for (int i = 0; i < 16; ++i) rl->rowptr[i + 1] = rl->rowptr[i] + __popc(ps->mask[i]);
-    }
-  }
-  __syncthreads();
-  if (ps->on && threadIdx.x < 16) {
-    int k = rl->rowptr[threadIdx.x];
-    for (int j = 0; j < 16; ++j)
-      if ((ps->mask[threadIdx.x] >> j) & 1u) {
-        reinterpret_cast<double*>(sS)[k] = ps->R[threadIdx.x * 16 + j];
+    const unsigned ball = __ballot_sync(0xffffffffu, keep);
+    const int row = e / D, j = e % D;
+    if (e < D * D && j == 0) rl->mask[row] = (ball >> (e & 31)) & ((1u << D) - 1u);
+    __syncthreads();
+    if (e < D * D) {
+      int off = 0;
+      for (int r = 0; r < row; ++r) off += __popc(rl->mask[r]);
+      if (keep) {
+        const int k = off + __popc(rl->mask[row] & ((1u << j) - 1u));
+        sS[k] = v;
         rl->col[k] = (unsigned char)j;
-        ++k;
       }
+      if (j == 0) rl->rowptr[row] = off;
+      if (e == D * D - 1) rl->rowptr[D] = off + __popc(rl->mask[row]);
+    }
   }
+  if (threadIdx.x == 0) *pauli_on = pauli ? 1 : 0;
   __syncthreads();
 }
 
@@ -605,11 +769,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
   __shared__ BBlk s_blk;
   __shared__ RowLists s_rl;
   __shared__ Tile16 s_t16;
-  __shared__ PauliStage s_ps;  // Pauli-basis decision and R' of the staged block
+  __shared__ int s_pauli;  // the staged block's tile items run in the Pauli basis
   __shared__ int s_idx;
   constexpr bool kF64 = sizeof(T2) == 16;
+  // thread 0 takes each item's ticket one item ahead, so the atomic's round
+  // trip overlaps the current item (tickets are monotone and every wait is
+  // on a smaller ticket, so the smallest unfinished item can always run)
+  int next = 0;
+  if (threadIdx.x == 0) next = atomicAdd(ticket, 1);
   for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(ticket, 1);
+    if (threadIdx.x == 0) {
+      s_idx = next;
+      next = atomicAdd(ticket, 1);
+    }
     __syncthreads();
     const int idx = s_idx;
     __syncthreads();
@@ -623,7 +795,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
       const int N = 1 << (2 * n);
       for (int e = threadIdx.x; e < N; e += blockDim.x) sR[e] = Cx<T2>::ldcg(&rho[e]);
       for (int b = it.tile0; b < it.tile0 + it.ntiles; ++b) {
-        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16, &s_ps, false);
+        stage_block(&blks[jb.block0 + b], &s_blk, sS, &s_rl, &s_t16, &s_pauli, false);
         const ApplyParams& p = s_blk.p;
         for (unsigned long long g = threadIdx.x; g < p.n_canon; g += blockDim.x) {
           if constexpr (kF64) {
@@ -648,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
     }
     // tile item: stage the block (independent of earlier blocks), then wait
     // until every tile of the previous block of this job is done
-    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16, &s_ps, true);
+    stage_block(&blks[jb.block0 + it.block], &s_blk, sS, &s_rl, &s_t16, &s_pauli, true);
     if (threadIdx.x == 0 && it.block > 0) {
       const int need = jb.never_ready ? 0x7fffffff : s_blk.tile_prefix;
       long long spins = 0;
@@ -677,7 +849,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         for (unsigned long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
           if (p.width == 1)
             apply_group_lists_global<1, true>(rho64, g, p, val, s_rl, mine);
-          else if (s_ps.on)
+          else if (s_pauli)
             apply_group_pauli_global(rho64, g, p, reinterpret_cast<const double*>(sS), s_rl, mine);
           else
             apply_group_lists_global<2, true>(rho64, g, p, val, s_rl, mine);
@@ -689,19 +861,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_apply(char* arena, const 
         const unsigned long long total = Mt * (Mt + 1) / 2;
         const unsigned long long u0 = (unsigned long long)it.tile0 * upt;
         const unsigned long long u1 = min(total, u0 + (unsigned long long)it.ntiles * upt);
-        for (unsigned long long u = u0; u < u1; ++u) {
-          if (p.width == 1)
-            apply_tile16<1>(rho, u, p, sS, s_t16);
-          else
-            apply_tile16<2>(rho, u, p, sS, s_t16);
+        if (p.width == 2 && s_pauli) {
+          apply_tiles16_pauli(rho, u0, u1, p, reinterpret_cast<const float*>(sS), s_t16);
+        } else {
+          for (unsigned long long u = u0; u < u1; ++u) {
+            if (p.width == 1)
+              apply_tile16<1>(rho, u, p, sS, s_t16);
+            else
+              apply_tile16<2>(rho, u, p, sS, s_t16);
+          }
         }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(&counters[it.job], it.ntiles);
-    }
+    // publish the item's writes (the barrier orders them before this
+    // thread's release) and count its tiles
+    if (threadIdx.x == 0)
+      asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(&counters[it.job]), "r"(it.ntiles) : "memory");
   }
 }
 

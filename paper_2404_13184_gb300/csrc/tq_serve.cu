@@ -83,6 +83,9 @@ struct Req {
   size_t rho_off = 0, rho_bytes = 0;
   size_t tab_off = 0, tab_bytes = 0;
   size_t o_sops = 0, o_sb = 0, o_sb64 = 0;  // within the table allocation
+  size_t o_pwork = 0, o_pauli = 0;          // Pauli-basis records and their sb64 offsets
+  std::vector<long long> blk_rec;           // per block: its Pauli record, or -1
+  std::vector<unsigned long long> rec_sb;   // per record: its block's sb64 offset
   int next_block = 0;
   int state = 0;  // 0 queued, 1 live, 2 done
   double result[2 + 16] = {};
@@ -174,9 +177,10 @@ int quantum(int n) {
 }
 
 // Layout of a request's table allocation: the uploaded blob, the per-op
-// superoperators, the fused FP64 superoperators and (split) their FP32
-// copies. Sets r.o_sops, r.o_sb and r.tab_bytes; returns the FP64 fused
-// table's offset.
+// superoperators, the fused FP64 superoperators, (split) their FP32 copies,
+// and the Pauli-basis records of its width-2 blocks with their sb64
+// offsets. Sets r.o_sops, r.o_sb, r.o_pwork, r.o_pauli and r.tab_bytes;
+// returns the FP64 fused table's offset.
 size_t table_layout(int prec, Req& r) {
   size_t off = align_up(r.prog.blob_bytes, 256);
   r.o_sops = off;
@@ -186,8 +190,25 @@ size_t table_layout(int prec, Req& r) {
   off = align_up(off + r.t.sb_entries * sizeof(double2), 256);
   r.o_sb = prec == TQ_FP64 ? o_sb64 : off;
   if (prec == TQ_SPLIT) off = align_up(off + r.t.sb_entries * sizeof(float2), 256);
+  r.o_pwork = off;
+  off = align_up(off + r.rec_sb.size() * sizeof(unsigned long long), 256);
+  r.o_pauli = off;
+  off = align_up(off + r.rec_sb.size() * sizeof(PauliRec), 256);
   r.tab_bytes = off;
   return o_sb64;
+}
+
+// Pauli-basis records for the width-2 blocks of a request that runs as a
+// tile job of the batch kernel (not resident in shared memory, not direct).
+void plan_pauli(const tq_server* s, Req& r) {
+  r.blk_rec.assign(r.prog.params.size(), -1);
+  r.rec_sb.clear();
+  if (is_resident(r.n, s->prec) || direct_request(s, r.n)) return;
+  for (size_t k = 0; k < r.prog.params.size(); ++k)
+    if (r.prog.params[k].width == 2) {
+      r.blk_rec[k] = (long long)r.rec_sb.size();
+      r.rec_sb.push_back((unsigned long long)r.prog.sb_off[k]);
+    }
 }
 
 // Admit the request: allocate, upload its tables, build + fuse, reset rho.
@@ -206,6 +227,13 @@ tq_status admit(tq_server* s, Req& r, char* stage, size_t* stage_used) {
   pack_blob(P, r.t, h);
   *stage_used = align_up(*stage_used + P.blob_bytes, 256);
   cudaError_t e = cudaMemcpyAsync(tab, h, P.blob_bytes, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess && !r.rec_sb.empty()) {
+    char* hw = stage + *stage_used;
+    const size_t bytes = r.rec_sb.size() * sizeof(unsigned long long);
+    std::memcpy(hw, r.rec_sb.data(), bytes);
+    *stage_used = align_up(*stage_used + bytes, 256);
+    e = cudaMemcpyAsync(tab + r.o_pwork, hw, bytes, cudaMemcpyHostToDevice, s->stream);
+  }
   if (e == cudaSuccess && P.n_uops > 0) {
     e = launch_build_superops(reinterpret_cast<const double2*>(tab + P.o_kraus), reinterpret_cast<const OpDesc*>(tab + P.o_ops),
                               (int)P.n_uops, P.max_dim2, reinterpret_cast<double2*>(tab + r.o_sops), s->stream);
@@ -214,6 +242,10 @@ tq_status admit(tq_server* s, Req& r, char* stage, size_t* stage_used) {
                       reinterpret_cast<const BlockDesc*>(tab + P.o_blk), reinterpret_cast<const MemberDesc*>(tab + P.o_mem),
                       reinterpret_cast<const FuseWork*>(tab + P.o_work), P.n_work, reinterpret_cast<double2*>(tab + o_sb64),
                       s->prec == TQ_SPLIT ? reinterpret_cast<float2*>(tab + r.o_sb) : nullptr, s->stream);
+    if (e == cudaSuccess)
+      e = launch_pauli_lists(reinterpret_cast<const double2*>(tab + o_sb64),
+                             reinterpret_cast<const unsigned long long*>(tab + r.o_pwork), (int)r.rec_sb.size(),
+                             s->prec == TQ_FP64 ? 0 : 1, reinterpret_cast<PauliRec*>(tab + r.o_pauli), s->stream);
   }
   if (e == cudaSuccess)
     e = launch_init_zero_state(static_cast<char*>(s->rho_mem.ptr) + r.rho_off, r.n, s->prec, s->stream);
@@ -301,6 +333,7 @@ tq_status tq_server_submit(tq_server* s, int n_qubits, const tq_op* ops, size_t 
   if (st != TQ_OK) return st;
   // its tables must fit the table arena on their own, or it would block the
   // FIFO head forever
+  plan_pauli(s, r);
   table_layout(s->prec, r);
   if (align_up(r.tab_bytes, 256) > s->tab_budget) return TQ_ERR_OOM;
   for (int m = 0; m < n_masks; ++m) r.masks.push_back(masks[m]);
@@ -365,7 +398,8 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
     size_t probe_live = s->live.size();
     for (int id : s->queue) {
       if ((int)probe_live >= s->max_live) break;
-      stage_need += align_up(s->reqs[id].prog.blob_bytes, 256);
+      const Req& q = s->reqs[id];
+      stage_need += align_up(q.prog.blob_bytes, 256) + align_up(q.rec_sb.size() * sizeof(unsigned long long), 256);
       admit_ids.push_back(id);
       ++probe_live;
     }
@@ -409,13 +443,14 @@ tq_status launch_tick(tq_server* s, int* n_live, int* n_queued) {
     for (size_t m = 0; m < r.masks.size(); ++m) j.masks[m] = r.masks[m];
     const size_t esz = s->prec == TQ_FP64 ? sizeof(double2) : sizeof(float2);
     const char* sb = static_cast<const char*>(s->tab_mem.ptr) + r.tab_off + r.o_sb;
-    const double2* sb64 = reinterpret_cast<const double2*>(static_cast<const char*>(s->tab_mem.ptr) + r.tab_off + r.o_sb64);
+    const PauliRec* recs =
+        reinterpret_cast<const PauliRec*>(static_cast<const char*>(s->tab_mem.ptr) + r.tab_off + r.o_pauli);
     for (int b = r.next_block; b < r.next_block + cnt; ++b) {
       BBlk bb;
       std::memset(&bb, 0, sizeof(bb));
       bb.p = r.prog.params[b];
       bb.S = sb + (size_t)r.prog.sb_off[b] * esz;
-      bb.S64 = sb64 + r.prog.sb_off[b];
+      bb.pauli = r.blk_rec[b] < 0 ? nullptr : recs + r.blk_rec[b];
       blks.push_back(bb);
     }
     set_tiles(blks.data() + j.block0, cnt, j.tile_log2, j.herm != 0, tiled16_job(r.n, s->prec));

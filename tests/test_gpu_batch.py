@@ -104,9 +104,9 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
     """Flops and HBM bytes tq_batch_work must report for one job, from the
     plan's blocks: every job runs its canonical groups (Hermitian mode);
     FP64 counts nonzeros (a diagonal block has D of them), split counts all;
-    FP64 width-2 blocks of tile jobs that the kernel runs in the Pauli basis
-    (when that is cheaper than 4 per nonzero of S) count 4 per nonzero of R'
-    plus 128."""
+    width-2 blocks of tile jobs that the kernel runs in the Pauli basis count
+    4 per real-times-complex product plus 128: FP64 per nonzero of R' (when
+    that is cheaper than 4 per nonzero of S), split always, dense (256)."""
     esz = 16 if precision == "fp64" else 8
     resident = esz * 4 ** n <= 64 * 1024
     herm = True
@@ -116,10 +116,13 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
         groups = M * (M + 1) // 2 if herm else 4 ** (n - w)
         nnz = 4 ** w if (precision == "fp64" and diagonal_fp64) else 16 ** w
         per = 8 * nnz
-        if precision == "fp64" and not resident and w == 2:
-            nr = _pauli_nonzeros(S)
-            if 2 * nr + 128 < 4 * nnz:
-                per = 4 * nr + 128
+        if not resident and w == 2:
+            if precision == "split":
+                per = 4 * 256 + 128
+            else:
+                nr = _pauli_nonzeros(S)
+                if 2 * nr + 128 < 4 * nnz:
+                    per = 4 * nr + 128
         flops += per * groups
         if not resident:
             bytes_ += ((4 ** n + 2 ** n) if herm else 2 * 4 ** n) * esz
