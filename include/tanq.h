@@ -380,8 +380,10 @@ void tq_batch_free(tq_batch* b);
 
 /* Autotuner of the batch engine: times every (fusion width in {1, 2},
  * entries per tile) candidate for n_qubits (2..14) at this precision on a
- * synthetic batch of random depolarised {H, RZ, RX, CX} circuits (about
- * 2^24 density-matrix entries in total, depth 64) and returns the fastest
+ * synthetic batch of random depolarised {H, RZ, RX, CX} circuits (depth
+ * 64; about 2^24 density-matrix entries in total, and at least enough jobs
+ * for ~8 work items per SM at the largest tile, at most 256) and returns
+ * the fastest
  * (*ms_out: its time per run). With cache_path not NULL, a cached result for
  * this GPU name, precision and n is returned without timing, and a new
  * result is appended to the file ("<gpu> <precision> <n> <tile_log2>

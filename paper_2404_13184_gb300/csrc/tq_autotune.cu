@@ -111,8 +111,17 @@ extern "C" tq_status tq_autotune(int precision, int n_qubits, const char* cache_
     if (ms_out) *ms_out = best_ms;
     return TQ_OK;
   }
-  // a synthetic batch of about 2^24 density-matrix entries in total
-  const int jobs = (int)std::max(1ll, std::min(256ll, (1ll << 24) >> (2 * n_qubits)));
+  // a synthetic batch of about 2^24 density-matrix entries in total, and at
+  // least enough jobs that the largest tile candidate (2^16 entries) still
+  // gives ~8 work items per SM and fusion round (two resident CTAs each, four
+  // items apiece); otherwise large registers would be tuned on a batch that
+  // leaves most of the GPU idle at large tiles
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return TQ_ERR_CUDA;
+  const long long tiles_per_block = std::max(1ll, (1ll << (2 * n_qubits - 1)) >> 16);  // canonical half / 2^16
+  const long long by_items = (8ll * sms + tiles_per_block - 1) / tiles_per_block;
+  const int jobs = (int)std::max(1ll, std::min(256ll, std::max((1ll << 24) >> (2 * n_qubits), by_items)));
   Rng rng{0x243F6A8885A308D3ull ^ (unsigned long long)(n_qubits * 131 + precision)};
   std::vector<std::vector<tq_op>> circuits;
   for (int j = 0; j < jobs; ++j) circuits.push_back(synth_circuit(n_qubits, 64, rng));
