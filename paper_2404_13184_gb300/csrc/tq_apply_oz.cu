@@ -131,6 +131,17 @@ __device__ __forceinline__ uint32_t digit_pair(unsigned long long fr, unsigned l
   return d;
 }
 
+// The same for two digits of one 32-bit word at once: one byte permute
+// gathers (Re, Im) of bytes ka and kb, one more per digit places them under
+// the FP16 1024 pattern.
+__device__ __forceinline__ void digit_pair2(uint32_t r, uint32_t i, int ka, int kb, uint32_t sgn, uint32_t nsg,
+                                            uint32_t& da, uint32_t& db) {
+  const uint32_t w = __byte_perm(r, i, (uint32_t)(ka | ((4 + ka) << 4) | (kb << 8) | ((4 + kb) << 12)));
+  const uint32_t wa = __byte_perm(w, 0x64646464u, 0x5140u), wb = __byte_perm(w, 0x64646464u, 0x5342u);
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(da) : "r"(wa), "r"(sgn), "r"(nsg));
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(db) : "r"(wb), "r"(sgn), "r"(nsg));
+}
+
 // Stores the digit words of 4 consecutive complex entries (one 16-byte chunk
 // of every digit operand's row); bit e of conj: entry e is conjugated (its
 // imaginary sign flipped in the digits).
@@ -145,13 +156,11 @@ __device__ __forceinline__ void store_chunk(const double2 x[4], uint32_t conj, i
     // FP16 sign bits of both halves
     const uint32_t sign = ((rh & 0x80000000u) >> 16) | ((ih ^ (((conj >> e) & 1u) << 31)) & 0x80000000u);
     const uint32_t sgn = 0x3c003c00u ^ sign, nsg = 0xe480e480u ^ sign;  // FP16 +-1 and -+1152 per half
-    w[0][e] = digit_pair<0>(fr, fi, sgn, nsg);
-    w[1][e] = digit_pair<1>(fr, fi, sgn, nsg);
-    w[2][e] = digit_pair<2>(fr, fi, sgn, nsg);
-    w[3][e] = digit_pair<3>(fr, fi, sgn, nsg);
-    w[4][e] = digit_pair<4>(fr, fi, sgn, nsg);
-    w[5][e] = digit_pair<5>(fr, fi, sgn, nsg);
-    w[6][e] = digit_pair<6>(fr, fi, sgn, nsg);
+    const uint32_t rh2 = (uint32_t)(fr >> 32), ih2 = (uint32_t)(fi >> 32), rl2 = (uint32_t)fr, il2 = (uint32_t)fi;
+    digit_pair2(rh2, ih2, 2, 1, sgn, nsg, w[0][e], w[1][e]);  // bytes 6, 5
+    w[2][e] = digit_pair<2>(fr, fi, sgn, nsg);                // byte 4
+    digit_pair2(rl2, il2, 3, 2, sgn, nsg, w[3][e], w[4][e]);  // bytes 3, 2
+    digit_pair2(rl2, il2, 1, 0, sgn, nsg, w[5][e], w[6][e]);  // bytes 1, 0
   }
 #pragma unroll
   for (int i = 0; i < kDigits; ++i) sts128(row_chunk + i * digit_bytes, w[i][0], w[i][1], w[i][2], w[i][3]);
@@ -239,17 +248,16 @@ __device__ __forceinline__ double recombine(const float c[kAccs], int scale, uin
   Z = mad_wide(b7, 1u, Z);
   // |Z| normalised to bit 63, rounded to 53 bits (a carry into bit 53 lands
   // in the exponent field), placed under the biased exponent 1086 - lz +
-  // scale; zero and results below the normal range give 0
+  // scale; zero (lz = 64, shifted by 0) and results below the normal range
+  // give 0, selected at the end without a branch
   const unsigned long long sm = (unsigned long long)((long long)Z >> 63);
   unsigned long long a = (Z ^ sm) - sm;
-  if (a == 0ull) return 0.0;
   const int lz = __clzll((long long)a);
-  a <<= lz;
-  const unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);
+  const unsigned long long an = a << (lz & 63);
+  const unsigned long long mant = (an >> 11) + ((an >> 10) & 1ull);
   const int eb = 1085 - lz + scale;  // biased exponent - 1 (mant carries the leading 1)
-  if (eb < 0) return 0.0;
-  return __longlong_as_double(
-      (long long)((((sm & 0x80000000ull) ^ neg) << 32) + ((unsigned long long)eb << 52) + mant));
+  const unsigned long long bits = ((((sm & 0x80000000ull) ^ neg) << 32) + ((unsigned long long)eb << 52) + mant);
+  return __longlong_as_double((a == 0ull || eb < 0) ? 0ll : (long long)bits);
 }
 
 struct Group {
@@ -345,40 +353,39 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
   // those read from their transposes are conjugated in the digits). A
   // group below the diagonal of a diagonal tile (not canonical) reads its
   // in-range entries too; its outputs are never written.
-  auto load = [&](const Group& g, double2 x[H]) {
+  auto load = [&](const Group& g, double2 x[H], uint32_t& conj) {
+    conj = 0;
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       bool up;
       x[l] = rho[entry_index(g.rb, g.cb, l, b0, b1, N, &up)];
+      conj |= (up ? 0u : 1u) << l;
     }
   };
 
   unsigned long long u = blockIdx.x;
   Group gn{};
   double2 xn[H];
+  uint32_t conjn = 0;
   if (u < n_units) {
     gn = group_of(u);
-    load(gn, xn);
+    load(gn, xn, conjn);
   }
   uint32_t phase = 0;
 #pragma unroll 1
   for (; u < n_units; u += gridDim.x, phase ^= 1u) {
     const Group g = gn;
+    const uint32_t conj = conjn;
     double2 x[H];
 #pragma unroll
     for (int l = 0; l < H; ++l) x[l] = xn[l];
     if (u + gridDim.x < n_units) {
       gn = group_of(u + gridDim.x);
-      load(gn, xn);
+      load(gn, xn, conjn);
     }
-    uint32_t mx = 0, conj = 0;
+    uint32_t mx = 0;
 #pragma unroll
-    for (int l = 0; l < H; ++l) {
-      bool up;
-      (void)entry_index(g.rb, g.cb, l, b0, b1, N, &up);
-      conj |= (up ? 0u : 1u) << l;
-      mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
-    }
+    for (int l = 0; l < H; ++l) mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
     s_E[tid] = mx;
     __syncthreads();  // both halves' maxima (and the previous unit's TMEM reads are done)
     const int E = max((int)(max(mx, s_E[tid ^ 128]) >> 20), 64);
