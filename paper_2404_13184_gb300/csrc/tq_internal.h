@@ -70,8 +70,11 @@ tq_status resolve_op(const tq_op& op, ResolvedOp* out);
 // by the FP64 pipe, so merging ops into blocks of up to 2 qubits is free.
 constexpr int kPlanF64Tensor = 16;
 // Relative pass time of the tensor-core FP64 engine against an HBM-bound
-// pass at the copy bandwidth (measured on GB300).
-constexpr double kTensorF64PassFactor = 2.9;
+// pass at the copy bandwidth, in the cost model's units (measured on GB300:
+// a 15-qubit width-2 pass takes 5.46 ms against 18.05 ms for the DFMA
+// row-list pass of the same 80-nonzero block, which the model prices at 40
+// flops per entry at the DFMA rate: 0.302 x (40 / 1.2e12) / (32 / 6.8e12)).
+constexpr double kTensorF64PassFactor = 2.14;
 
 // Per-precision cost (arbitrary units per 4^n entries) of one apply pass of
 // a block of the given width; nnz < 0 means dense. Used by the automatic
