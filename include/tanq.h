@@ -368,9 +368,10 @@ tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size
  * Hermitian mode), 8 real flops per complex multiply-add the apply kernel
  * issues -- FP64 counts nonzero superoperator entries only (its row lists
  * skip the zeros), split counts all -- except for width-2 blocks of tile
- * jobs that the kernel runs in the Pauli basis (real R', rows of nonzeros),
- * which count 4 flops per nonzero of R' plus the 128 adds of the basis
- * changes. bytes: what the apply passes must move through
+ * jobs that the kernel runs in the Pauli basis (real R' = T S T^dagger /
+ * 16): FP64 row lists of R' count 4 flops per nonzero plus the 128 adds of
+ * the basis changes, split (always in the Pauli basis, R' dense) 4 x 256 +
+ * 128. bytes: what the apply passes must move through
  * HBM: per block of a tile job one read and one write of the stored entries
  * (the upper triangle in Hermitian mode), per resident job one load and one
  * store of vec(rho). TQ_ERR_STATE before the first run; waits for the run. */
