@@ -443,7 +443,24 @@ def split_accuracy(tq, n=8, steps=30):
     return {"qubits": n, "steps": steps, "zz_max_abs_err_vs_fp64": max(abs(a - b) for a, b in zip(z32, z64)),
             "max_abs_rho_diff_vs_fp64": float(np.max(np.abs(r32 - r64))),
             "split_trace_drift": abs(t32 - 1.0), "fp64_trace_drift": abs(t64 - 1.0),
-            "split_min_eigenvalue": min_eig(r32), "fp64_min_eigenvalue": min_eig(r64)}
+            "split_min_eigenvalue": min_eig(r32), "fp64_min_eigenvalue": min_eig(r64),
+            "_zz64": z64, "_zz32": z32}
+
+
+def oracle_tfim_zz(n=8, steps=30):
+    """<Z0 Z1> after each Trotter step of the same ring TFIM on n qubits from
+    the CPU oracle (the config's oracle comparison; run in the CPU-baseline
+    leg only)."""
+    from oracle import dm_oracle
+    from paper_2404_13184_gb300 import workloads
+    c = workloads.tfim_ring(n, steps)
+    rho = dm_oracle.zero_state(n)
+    zz = []
+    for a, b in c.steps:
+        for op in c.ops[a:b]:
+            rho = dm_oracle.apply_op(rho, op)
+        zz.append(float(dm_oracle.expect_z(rho, ZZ_MASK)))
+    return zz
 
 
 def autotune_cache():
@@ -1070,6 +1087,13 @@ def main():
                                       "peak_source": f"{peak_src} HBM copy bandwidth"},
                          "gpu_launches": split["launches"]}
     with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if split is not None:
+        acc = line["split"]["accuracy_8q"]
+        z64, z32 = acc.pop("_zz64"), acc.pop("_zz32")
+        if with_cpu:
+            zo = oracle_tfim_zz(acc["qubits"], acc["steps"])
+            acc["fp64_zz_max_abs_err_vs_oracle"] = max(abs(a - b) for a, b in zip(z64, zo))
+            acc["split_zz_max_abs_err_vs_oracle"] = max(abs(a - b) for a, b in zip(z32, zo))
     if world == 1 and not args.no_extras:
         line.update(extras(tq, torch, args, with_cpu))
     if with_cpu:

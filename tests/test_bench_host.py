@@ -51,3 +51,17 @@ def test_served_speedup_counts_only_completed_requests():
     assert abs(r["plain_fp64_s_for_completed"] - 0.5) < 1e-12   # 100 x 1 ms + 200 x 2 ms
     assert abs(r["speedup_vs_plain_fp64"] - 0.25) < 1e-12
     assert abs(r["plain_fp64_circuits_per_s"] - 4.0) < 1e-12
+
+
+def test_oracle_tfim_zz_reads_each_step_of_the_ring_circuit():
+    # one <Z0 Z1> per Trotter step, equal to the oracle run step by step
+    zz = bench.oracle_tfim_zz(4, 3)
+    c = W.tfim_ring(4, 3)
+    rho = O.zero_state(4)
+    want = []
+    for a, b in c.steps:
+        for op in c.ops[a:b]:
+            rho = O.apply_op(rho, op)
+        want.append(float(O.expect_z(rho, bench.ZZ_MASK)))
+    assert zz == want and len(zz) == 3
+    assert all(abs(z) <= 1.0 for z in zz) and zz[0] > 0.9   # |0000> starts at <Z0 Z1> = 1; small dt
