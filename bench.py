@@ -509,11 +509,14 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11
         err["max_abs_trace_diff_vs_fp64"] = max(abs(r[0] - f[0]) for r, f in zip(results, reference))
     info = b.info()
     work = b.work()
+    tensor_jobs = b.tensor_jobs() if precision == "fp64" else 0
     b.free()
     # roofline of the whole run (graph replay incl. superoperator build, fusion
-    # and readout): FP64 against the DFMA rate, split against HBM bandwidth
+    # and readout): split, and FP64 whose tile jobs run on the tensor-core
+    # pass (nearly all the bytes), against HBM bandwidth; FP64 on the DFMA
+    # engine against the DFMA rate
     hbm_gbs, sm_max, src = peaks()
-    if precision == "fp64":
+    if precision == "fp64" and tensor_jobs == 0:
         ach = work["flops"] / (ms / 1e3) / 1e12
         sms = device_sms()
         peak = fp64_peak_tflops(sm_max, sms)
@@ -529,6 +532,9 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11
         ach = work["bytes"] / (ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs,
                 "bytes_per_run": work["bytes"], "peak_source": f"hbm_gbs ({src})"}
+        if precision == "fp64":
+            roof["tensor_core_jobs"] = tensor_jobs
+            roof["flops_per_run"] = work["flops"]
     gates = sum(c.n_gates for c in circuits)
     cpu = None
     if with_cpu:

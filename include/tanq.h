@@ -337,15 +337,29 @@ tq_status tq_batch_add(tq_batch* b, int n_qubits, const tq_op* ops, size_t n_ops
  * granularity of the persistent kernel, normally set by the autotuner. */
 tq_status tq_batch_set_tile(tq_batch* b, int n_qubits, int tile_log2);
 
+/* FP64 engine of the batch's tile jobs (vec(rho) > 64 KiB), as for single
+ * states (tq_fp64_engine; default TQ_ENGINE_AUTO). With the tensor-core
+ * engine, a tile job whose blocks are all of width <= 2 on at least 6
+ * qubits runs on the batched FP64-accurate tensor-core pass instead of the
+ * persistent kernel: one launch per fusion round, each applying that
+ * round's block of every such job (tq_set_fp64_engine describes the
+ * arithmetic). Resident jobs and split batches are unaffected. Takes effect
+ * at the next run. */
+tq_status tq_batch_set_fp64_engine(tq_batch* b, int engine);
+
+/* Jobs of the last planned run that ran on the batched tensor-core pass. */
+tq_status tq_batch_tensor_jobs(const tq_batch* b, size_t* n_jobs);
+
 /* Enqueue one run of every job (asynchronous). */
 tq_status tq_batch_run(tq_batch* b);
 
 /* Failure-detection hook for tests: every device-side wait of the batch
  * kernel gives up after max_spin polls (default 2e7, seconds), sets an error
  * flag and lets the kernel finish; with never_ready_job >= 0 that job's waits
- * can never be satisfied, so a run ends with TQ_ERR_TIMEOUT from
- * tq_batch_wait while the CUDA context stays usable. -1 restores normal
- * waits. */
+ * can never be satisfied (the job stays on the persistent kernel), so a run
+ * ends with TQ_ERR_TIMEOUT from tq_batch_wait while the CUDA context stays
+ * usable. -1 restores normal waits. The tensor-core pass's waits follow
+ * tq_test_tc_wait_limit and report through tq_batch_wait too. */
 tq_status tq_batch_test_wait_limit(tq_batch* b, long long max_spin, int never_ready_job);
 
 /* Wait for the last run; TQ_ERR_TIMEOUT if a bounded device-side wait ran
@@ -359,7 +373,8 @@ tq_status tq_batch_result(tq_batch* b, int job, double* out);
 /* vec(rho_job) as 2*4^n interleaved doubles (waits for the run). */
 tq_status tq_batch_get_rho(tq_batch* b, int job, double* out);
 
-/* Jobs, work items of the persistent launch, bytes of all density matrices. */
+/* Jobs, work items of the persistent launch (tensor-core jobs not
+ * included), bytes of all density matrices. */
 tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size_t* rho_bytes);
 
 /* Algorithmic work of one run, counted on the device from the fused
@@ -371,7 +386,8 @@ tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size
  * jobs that the kernel runs in the Pauli basis (real R' = T S T^dagger /
  * 16): FP64 row lists of R' count 4 flops per nonzero plus the 128 adds of
  * the basis changes, split (always in the Pauli basis, R' dense) 4 x 256 +
- * 128. bytes: what the apply passes must move through
+ * 128; blocks of jobs on the tensor-core pass count the dense product (8
+ * per entry of S). bytes: what the apply passes must move through
  * HBM: per block of a tile job one read and one write of the stored entries
  * (the upper triangle in Hermitian mode), per resident job one load and one
  * store of vec(rho). TQ_ERR_STATE before the first run; waits for the run. */

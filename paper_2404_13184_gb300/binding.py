@@ -83,6 +83,8 @@ _SIGNATURES = [
     ("tq_batch_set_tile", c_int, [c_void_p, c_int, c_int]),
     ("tq_batch_run", c_int, [c_void_p]),
     ("tq_batch_test_wait_limit", c_int, [c_void_p, ctypes.c_longlong, c_int]),
+    ("tq_batch_set_fp64_engine", c_int, [c_void_p, c_int]),
+    ("tq_batch_tensor_jobs", c_int, [c_void_p, POINTER(c_size_t)]),
     ("tq_test_tc_wait_limit", c_int, [ctypes.c_longlong, c_int]),
     ("tq_batch_wait", c_int, [c_void_p]),
     ("tq_batch_result", c_int, [c_void_p, c_int, POINTER(c_double)]),
@@ -209,7 +211,7 @@ class DeviceProgram:
 class Batch:
     """Many independent circuits run in one persistent launch (tq_batch)."""
 
-    def __init__(self, precision: str = "fp64", stream=None):
+    def __init__(self, precision: str = "fp64", stream=None, engine: str = "auto"):
         lib = load()
         self.precision = precision
         torch = _torch_plumbing()
@@ -219,6 +221,18 @@ class Batch:
         self._nmasks = []
         self._n = []
         _check(lib.tq_batch_create(PRECISION[precision], c_void_p(stream), ctypes.byref(self._h)), "tq_batch_create")
+        if engine != "auto":
+            self.set_fp64_engine(engine)
+
+    def set_fp64_engine(self, engine: str):
+        """FP64 engine of the tile jobs: "auto" (tensor cores), "dfma" or "tensor"."""
+        _check(_lib.tq_batch_set_fp64_engine(self._h, ENGINES[engine]), "tq_batch_set_fp64_engine")
+
+    def tensor_jobs(self) -> int:
+        """Jobs of the last planned run on the batched tensor-core pass."""
+        v = c_size_t(0)
+        _check(_lib.tq_batch_tensor_jobs(self._h, ctypes.byref(v)), "tq_batch_tensor_jobs")
+        return v.value
 
     def add(self, n: int, ops, width: int = -1, masks=()) -> int:
         prog = ops if isinstance(ops, Program) else Program(ops)

@@ -69,6 +69,7 @@
 #include "tq_device.cuh"
 #include "tanq.h"
 #include "tq_tc.cuh"
+#include "tq_oz.cuh"
 
 namespace tq {
 
@@ -454,6 +455,179 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_oz2(double2
   }
 }
 
+// Batched form of the pass: one fusion round of many independent states
+// (the batch engine's FP64 tile jobs), from a table of (state, block) jobs
+// whose units are numbered one after another. Each CTA takes a contiguous
+// range of units, so it crosses few job boundaries. At a boundary it
+// switches to the new job's tables, loads that job's first unit without
+// prefetch, and rebuilds the superoperator digits after the CTA barrier
+// that follows the previous unit's epilogue (every thread is then done with
+// the previous digits and row exponents). The per-unit work is the
+// single-state pass's.
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_batch_oz2(const OzJob* __restrict__ jobs, int n_jobs,
+                                                                      unsigned long long n_units_total,
+                                                                      unsigned long long chunk, long long max_tries,
+                                                                      int skip_mma) {
+  constexpr int H = 8;  // entries (and complex outputs) per thread
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t bar = sbase + kOffBar;
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kOffFlag);
+  const int* s_G = reinterpret_cast<const int*>(smem + kOffG);
+  uint32_t* s_E = reinterpret_cast<uint32_t*>(smem + kOffE);  // [2][128] half maxima
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  const int m = tid & 127, h = tid >> 7, wq = w & 3;
+  if (tid == 0) {
+    bar_init(bar, 1);
+    *s_abort = 0;
+  }
+  if (w == 0) tmem_alloc(sbase + kOffTmem, kTmemCols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  const uint64_t a_desc0 = smem_desc(sbase + kOffA), b_desc0 = smem_desc(sbase + kOffB);
+  const int i = (lane % 8) + 8 * (wq % 2), j0 = (lane / 8) + 4 * (wq / 2);
+  const uint32_t a_row = sbase + kOffA + core_off(m, 2 * h);
+  const uint32_t t_row = tmem + ((uint32_t)(32 * wq) << 16);
+
+  // the current job's tables
+  int jn = 0;
+  double2* rho = nullptr;
+  unsigned int b0 = 0, b1 = 0, N = 0, ch1 = 0, di = 0, dj0 = 0, dj1 = 0;
+  int qs[2] = {0, 0};
+  unsigned long long ubase = 0;
+  auto set_job = [&](unsigned long long uu) {
+    while (jn + 1 < n_jobs && jobs[jn + 1].unit0 <= uu) ++jn;
+    const OzJob& J = jobs[jn];
+    rho = J.rho;
+    qs[0] = min(J.p.q[0], J.p.q[1]);
+    qs[1] = max(J.p.q[0], J.p.q[1]);
+    b0 = 1u << J.p.q[0];
+    b1 = 1u << J.p.q[1];
+    N = 1u << J.p.n;
+    ch1 = h ? b1 : 0u;
+    di = (unsigned int)deposit_zeros(i, qs, 2);
+    dj0 = (unsigned int)deposit_zeros(j0, qs, 2);
+    dj1 = (unsigned int)deposit_zeros(j0 + 8, qs, 2);
+    ubase = J.unit0;
+  };
+  auto same_job = [&](unsigned long long uu) { return jn + 1 >= n_jobs || jobs[jn + 1].unit0 > uu; };
+  auto group_of = [&](unsigned long long uu) {
+    const unsigned long long v = uu - ubase;
+    bool diag = false;
+    const unsigned long long tt = canonical_group(v >> 1, 32, &diag);
+    const int j = (int)(v & 1ull) * 8 + j0;
+    Group g;
+    g.active = !(diag && i > j);
+    g.self = diag && i == j;
+    g.rb = (unsigned int)deposit_zeros((tt & 0xffffffffull) * kTile, qs, 2) + di;
+    g.cb = (unsigned int)deposit_zeros((tt >> 32) * kTile, qs, 2) + ((v & 1ull) ? dj1 : dj0) + ch1;
+    return g;
+  };
+  auto load = [&](const Group& g, double2 x[H], uint32_t& conj) {
+    conj = 0;
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      bool up;
+      x[l] = rho[entry_index(g.rb, g.cb, l, b0, b1, N, &up)];
+      conj |= (up ? 0u : 1u) << l;
+    }
+  };
+
+  unsigned long long u = (unsigned long long)blockIdx.x * chunk;
+  const unsigned long long u_end = min(u + chunk, n_units_total);
+  Group gn{};
+  double2 xn[H];
+  uint32_t conjn = 0;
+  bool have = false, need_b = true;
+  uint32_t phase = 0;
+#pragma unroll 1
+  for (; u < u_end; ++u, phase ^= 1u) {
+    if (!have) {  // first unit, or the first unit of the next job
+      set_job(u);
+      need_b = true;
+      gn = group_of(u);
+      load(gn, xn, conjn);
+    }
+    const Group g = gn;
+    const uint32_t conj = conjn;
+    double2 x[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) x[l] = xn[l];
+    have = u + 1 < u_end && same_job(u + 1);
+    if (have) {
+      gn = group_of(u + 1);
+      load(gn, xn, conjn);
+    }
+    uint32_t mx = 0;
+#pragma unroll
+    for (int l = 0; l < H; ++l) mx = max(mx, max(abs_hi(x[l].x), abs_hi(x[l].y)));
+    s_E[tid] = mx;
+    __syncthreads();  // both halves' maxima (and the previous unit's TMEM and s_G reads are done)
+    const int E = max((int)(max(mx, s_E[tid ^ 128]) >> 20), 64);
+    if (need_b) {
+      if (tid < 128) build_b_digits(smem, sbase, jobs[jn].S, jobs[jn].embed, tid);
+      need_b = false;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) store_chunk(x + 4 * c, conj >> (4 * c), E, a_row + c * 128u, kADigitBytes);
+    fence_operands();
+    fence_before_sync();
+    __syncthreads();
+    if (*s_abort) break;
+    if (tid == 0 && !skip_mma) {
+      fence_after_sync();
+#pragma unroll
+      for (int ia = 0; ia < kDigits; ++ia)
+#pragma unroll
+        for (int kh = 0; kh < 2; ++kh)
+          mma_bf16_n(tmem + (uint32_t)(32 * ia), a_desc0 + (uint64_t)((ia * kADigitBytes + kh * 256) >> 4),
+                     b_desc0 + (uint64_t)((kh * 256) >> 4), idesc_m128_f16(32 * (8 - ia)),
+                     (ia == 0 && kh == 0) ? 0u : 1u);
+      commit(bar);
+    }
+    const bool waited = bar_wait(bar, phase, max_tries);
+    if (!waited) {
+      atomicAdd(&g_oz_timeouts, 1u);
+      *s_abort = 1;
+    }
+    if (!__all_sync(0xffffffffu, waited)) continue;
+    fence_after_sync();
+#pragma unroll 1
+    for (int ch = 0; ch < 2; ++ch) {
+      uint32_t cv[kAccs][8];
+      load_accs(t_row, 16 * h + 8 * ch, cv);
+      if (!g.active) continue;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int o = H * h + 4 * ch + e;
+        float cr[kAccs], ci[kAccs];
+#pragma unroll
+        for (int a = 0; a < kAccs; ++a) {
+          cr[a] = __uint_as_float(cv[a][2 * e]);
+          ci[a] = __uint_as_float(cv[a][2 * e + 1]);
+        }
+        bool up;
+        const unsigned int idx = entry_index(g.rb, g.cb, 4 * ch + e, b0, b1, N, &up);
+        double2 y;
+        y.x = recombine(cr, E + s_G[2 * o] - 2096, 0u);
+        y.y = recombine(ci, E + s_G[2 * o + 1] - 2096, up ? 0u : 0x80000000u);
+        if (up || !g.self) rho[idx] = y;
+      }
+    }
+    fence_before_sync();
+  }
+  __syncthreads();
+  if (*s_abort && tid == 0) bar_wait(bar, phase ^ 1u, max_tries);
+  __syncthreads();
+  if (w == 0) {
+    fence_after_sync();
+    tmem_free(tmem, kTmemCols);
+  }
+}
+
 }  // namespace
 
 bool oz_eligible(int n, int width) { return (width == 1 || width == 2) && n - 2 >= 4; }
@@ -481,6 +655,46 @@ cudaError_t launch_herm_oz(double2* rho, const double2* S, const ApplyParams& p,
   const int grid = (int)std::max<unsigned long long>(
       1, std::min<unsigned long long>(n_units, (unsigned long long)num_sms * kCtasPerSm));
   k_apply_herm_oz2<<<grid, kThreads, kSmemBytes, st>>>(rho, S, q, embed, tries, skip);
+  return cudaGetLastError();
+}
+
+unsigned long long oz_units(int n) {
+  const unsigned long long Mt = (1ull << (n - 2)) / kTile;
+  return Mt * (Mt + 1);
+}
+
+bool oz_job(double2* rho, const double2* S, const ApplyParams& p, OzJob* out) {
+  if (!oz_eligible(p.n, p.width)) return false;
+  OzJob j{};
+  j.rho = rho;
+  j.S = S;
+  j.p = p;
+  if (p.width == 1) {  // S (x) I on (q, q'), q' the highest other qubit (as launch_herm_oz)
+    j.embed = 1;
+    j.p.width = 2;
+    j.p.q[1] = p.q[0] == p.n - 1 ? p.n - 2 : p.n - 1;
+  }
+  *out = j;
+  return true;
+}
+
+cudaError_t launch_batch_oz(const OzJob* jobs, int n_jobs, unsigned long long n_units, int num_sms,
+                            cudaStream_t st) {
+  if (n_jobs <= 0 || n_units == 0) return cudaSuccess;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(k_batch_oz2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  if (attr != cudaSuccess) return attr;
+  long long tries = 0;
+  int skip = 0;
+  tc_test_limits(&tries, &skip);
+  // persistent grid, each CTA a contiguous range of units
+  const unsigned long long slots = (unsigned long long)num_sms * kCtasPerSm;
+  const unsigned long long chunk = (n_units + slots - 1) / slots;
+  const int grid = (int)((n_units + chunk - 1) / chunk);
+  k_batch_oz2<<<grid, kThreads, kSmemBytes, st>>>(jobs, n_jobs, n_units, chunk, tries, skip);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "tq_batch_kernels.cuh"
+#include "tq_oz.cuh"
 
 using namespace tq;
 using namespace tq::batch;
@@ -35,6 +36,17 @@ struct tq_batch {
   DevBuf arena, blob, sops, sb64, sb32, djobs, dblks, ditems, counters, ctl, results;
   DevBuf pauli, pwork;  // Pauli-basis records of width-2 tile-job blocks and their sb64 offsets
   int n_pauli = 0;
+  // FP64 tile jobs on the batched tensor-core pass: one launch per fusion
+  // round over every such job's block of that round
+  int fp64_engine = TQ_ENGINE_AUTO;
+  struct OzRound {
+    size_t off;
+    int count;
+    unsigned long long units;
+  };
+  DevBuf ozjobs;
+  std::vector<OzRound> oz_rounds;
+  size_t n_tensor_jobs = 0;
   PinBuf host_out;  // results + error flag
   size_t n_items = 0;
   size_t arena_bytes = 0;
@@ -97,6 +109,7 @@ __global__ void k_batch_work(const BJob* __restrict__ jobs, const BBlk* __restri
     // basis changes
     unsigned long long per = 8ull * nnz;
     if (bk.pauli && bk.pauli->on) per = 4ull * (prec == 0 ? (unsigned long long)bk.pauli->nnz : 256ull) + 128;
+    if (jb.tensor) per = 8ull * D * D;  // the tensor-core pass: the dense product's algorithmic count
     const unsigned long long groups = jb.herm ? bk.p.n_canon : bk.p.n_groups;
     fl += per * groups;
     if (!jb.resident) by += (jb.herm ? N + R : 2 * N) * esz;
@@ -163,6 +176,15 @@ tq_status finalize(tq_batch* b) {
     // at least 16 groups' worth of entries per tile, at most 2^16 tiles per block
     hj.tile_log2 = std::min(std::max({tl, 4, 2 * J.n - 16}), 2 * J.n);
     hj.herm = batch_herm(J.n, b->prec) ? 1 : 0;
+    // FP64 tile jobs whose blocks are all eligible run on the batched
+    // tensor-core pass (with the tensor-core engine; a job under the
+    // never-ready test hook stays on the batch kernel, whose waits it tests)
+    hj.tensor = 0;
+    if (b->prec == TQ_FP64 && fp64_engine_is_tensor(b->fp64_engine) && !hj.resident && (int)j != b->never_ready_job) {
+      bool all = !J.prog.params.empty();
+      for (const ApplyParams& pp : J.prog.params) all = all && oz_eligible(pp.n, pp.width);
+      hj.tensor = all ? 1 : 0;
+    }
     hj.n_masks = (int)J.masks.size();
     hj.never_ready = (int)j == b->never_ready_job ? 1 : 0;
     for (size_t m = 0; m < J.masks.size(); ++m) hj.masks[m] = J.masks[m];
@@ -171,7 +193,7 @@ tq_status finalize(tq_batch* b) {
       std::memset(&bb, 0, sizeof(bb));
       bb.p = J.prog.params[k];
       bb.S = reinterpret_cast<const void*>(J.prog.sb_off[k] + sbb);  // offset; made absolute below
-      if (!hj.resident && bb.p.width == 2) {
+      if (!hj.resident && !hj.tensor && bb.p.width == 2) {
         blk_rec.push_back((long long)rec_sb.size());
         rec_sb.push_back((unsigned long long)(J.prog.sb_off[k] + sbb));
       } else {
@@ -197,7 +219,7 @@ tq_status finalize(tq_batch* b) {
   for (int r = 0; r < max_blocks; ++r)
     for (size_t j = 0; j < hjobs.size(); ++j) {
       const BJob& hj = hjobs[j];
-      if (hj.resident || r >= hj.n_blocks) continue;
+      if (hj.resident || hj.tensor || r >= hj.n_blocks) continue;
       const int tiles = hblks[hj.block0 + r].tiles;
       for (int t = 0; t < tiles; ++t) items.push_back(BItem{(int)j, r, t, 1});
     }
@@ -256,6 +278,37 @@ tq_status finalize(tq_batch* b) {
     e = cudaMemcpy(b->ditems.ptr, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !rec_sb.empty())
     e = cudaMemcpy(b->pwork.ptr, rec_sb.data(), rec_sb.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+  // the tensor-core rounds: round r holds block r of every tensor job that has one
+  b->oz_rounds.clear();
+  b->n_tensor_jobs = 0;
+  {
+    std::vector<OzJob> oz;
+    int rounds = 0;
+    for (const BJob& hj : hjobs)
+      if (hj.tensor) {
+        ++b->n_tensor_jobs;
+        rounds = std::max(rounds, hj.n_blocks);
+      }
+    for (int r = 0; r < rounds; ++r) {
+      tq_batch::OzRound rd{oz.size(), 0, 0};
+      for (size_t j = 0; j < hjobs.size(); ++j) {
+        const BJob& hj = hjobs[j];
+        if (!hj.tensor || r >= hj.n_blocks) continue;
+        const BBlk& bb = hblks[hj.block0 + r];
+        OzJob oj{};
+        oz_job(reinterpret_cast<double2*>(static_cast<char*>(b->arena.ptr) + hj.rho_off),
+               static_cast<const double2*>(bb.S), bb.p, &oj);
+        oj.unit0 = rd.units;
+        rd.units += oz_units(hj.n);
+        oz.push_back(oj);
+        ++rd.count;
+      }
+      b->oz_rounds.push_back(rd);
+    }
+    if (e == cudaSuccess) e = alloc(b->ozjobs, std::max<size_t>(1, oz.size()) * sizeof(OzJob));
+    if (e == cudaSuccess && !oz.empty())
+      e = cudaMemcpy(b->ozjobs.ptr, oz.data(), oz.size() * sizeof(OzJob), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) return to_status(e);
 
   const size_t smem = b->prec == TQ_FP64 ? apply_smem<double2>() : apply_smem<float2>();
@@ -308,6 +361,8 @@ tq_status finalize(tq_batch* b) {
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
   }
+  for (const tq_batch::OzRound& rd : b->oz_rounds)
+    launch_batch_oz(static_cast<const OzJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, st);
   if (b->prec == TQ_FP64)
     k_batch_reduce<double2><<<n_jobs, kThreads, 0, st>>>(static_cast<const char*>(b->arena.ptr),
                                                          static_cast<const BJob*>(b->djobs.ptr), 0,
@@ -382,6 +437,19 @@ tq_status tq_batch_set_tile(tq_batch* b, int n_qubits, int tile_log2) {
   return TQ_OK;
 }
 
+tq_status tq_batch_set_fp64_engine(tq_batch* b, int engine) {
+  if (!b || engine < TQ_ENGINE_AUTO || engine > TQ_ENGINE_TENSOR) return TQ_ERR_ARG;
+  b->fp64_engine = engine;
+  b->ready = false;
+  return TQ_OK;
+}
+
+tq_status tq_batch_tensor_jobs(const tq_batch* b, size_t* n_jobs) {
+  if (!b || !n_jobs) return TQ_ERR_ARG;
+  *n_jobs = b->ready ? b->n_tensor_jobs : 0;
+  return TQ_OK;
+}
+
 tq_status tq_batch_test_wait_limit(tq_batch* b, long long max_spin, int never_ready_job) {
   if (!b || max_spin < 1 || never_ready_job < -1 || never_ready_job >= (int)b->jobs.size()) return TQ_ERR_ARG;
   b->max_spin = max_spin;
@@ -407,7 +475,9 @@ tq_status tq_batch_wait(tq_batch* b) {
   if (!b->ready) return TQ_OK;
   const int err = *reinterpret_cast<const int*>(static_cast<const char*>(b->host_out.ptr) +
                                                 b->jobs.size() * kResults * sizeof(double));
-  return err ? TQ_ERR_TIMEOUT : TQ_OK;
+  unsigned int oz_timeouts = 0;
+  if (b->n_tensor_jobs && oz_take_timeouts(&oz_timeouts, b->stream) != cudaSuccess) return TQ_ERR_CUDA;
+  return err || oz_timeouts ? TQ_ERR_TIMEOUT : TQ_OK;
 }
 
 tq_status tq_batch_result(tq_batch* b, int job, double* out) {
@@ -474,7 +544,7 @@ void tq_batch_free(tq_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
-  for (DevBuf* d : {&b->arena, &b->blob, &b->sops, &b->sb64, &b->sb32, &b->djobs, &b->dblks, &b->ditems, &b->pauli, &b->pwork,
+  for (DevBuf* d : {&b->arena, &b->blob, &b->sops, &b->sb64, &b->sb32, &b->djobs, &b->dblks, &b->ditems, &b->pauli, &b->pwork, &b->ozjobs,
                     &b->counters, &b->ctl, &b->results})
     if (d->ptr) cudaFree(d->ptr);
   if (b->host_out.ptr) cudaFreeHost(b->host_out.ptr);

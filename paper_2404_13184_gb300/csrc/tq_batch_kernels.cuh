@@ -35,6 +35,7 @@ struct BJob {
   int n_masks;
   int never_ready;  // test hook: this job's waits can never be satisfied
   int herm;         // Hermitian mode: canonical groups only, rows <= columns kept
+  int tensor;       // FP64 tile job run by the batched tensor-core pass (not by the batch kernel)
   unsigned long long masks[kMaxMasks];
 };
 

@@ -106,7 +106,9 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
     FP64 counts nonzeros (a diagonal block has D of them), split counts all;
     width-2 blocks of tile jobs that the kernel runs in the Pauli basis count
     4 per real-times-complex product plus 128: FP64 per nonzero of R' (when
-    that is cheaper than 4 per nonzero of S), split always, dense (256)."""
+    that is cheaper than 4 per nonzero of S), split always, dense (256).
+    FP64 tile jobs on the batched tensor-core pass (the default engine)
+    count the dense product."""
     esz = 16 if precision == "fp64" else 8
     resident = esz * 4 ** n <= 64 * 1024
     herm = True
@@ -116,7 +118,9 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
         groups = M * (M + 1) // 2 if herm else 4 ** (n - w)
         nnz = 4 ** w if (precision == "fp64" and diagonal_fp64) else 16 ** w
         per = 8 * nnz
-        if not resident and w == 2:
+        if precision == "fp64" and not resident and n >= 6:
+            per = 8 * 16 ** w          # tensor-core pass: the dense algorithmic count
+        elif not resident and w == 2:
             if precision == "split":
                 per = 4 * 256 + 128
             else:
@@ -275,3 +279,33 @@ def test_autotune_picks_a_valid_candidate_and_caches(tq, tmp_path):
     b.run()
     for j in range(len(jobs)):
         assert np.array_equal(a.rho(j), b.rho(j))
+
+
+@pytest.mark.parametrize("engine", ["auto", "dfma"])
+def test_fp64_tile_jobs_on_either_engine_match_the_oracle(tq, engine):
+    # tile jobs (7-9 qubits) run on the batched tensor-core pass with the
+    # default engine, on the persistent kernel with "dfma"; resident jobs on
+    # the persistent kernel either way; one job alone equals itself in the mix
+    jobs = _jobs(12, 4, 9, 13, depth=(20, 60))
+    b = tq.Batch("fp64", engine=engine)
+    for n, ops, masks in jobs:
+        b.add(n, ops, width=-1, masks=masks)
+    b.run()
+    b.wait()
+    tiles = sum(1 for n, _, _ in jobs if 16 * 4 ** n > 64 * 1024)
+    assert b.tensor_jobs() == (tiles if engine == "auto" else 0)
+    for j, (n, ops, masks) in enumerate(jobs):
+        want = O.run_circuit(n, ops)
+        assert np.max(np.abs(b.rho(j) - want)) < TOL64, (j, n)
+        res = b.result(j)
+        for i, m in enumerate(masks):
+            assert abs(res[2 + i] - O.expect_z(want, m)) < TOL64
+    k = next(j for j, (n, _, _) in enumerate(jobs) if 16 * 4 ** n > 64 * 1024)
+    alone = tq.Batch("fp64", engine=engine)
+    alone.add(jobs[k][0], jobs[k][1], width=-1, masks=jobs[k][2])
+    alone.run()
+    alone.wait()
+    assert np.array_equal(alone.rho(0), b.rho(k))
+    alone.free()
+    b.free()
+
