@@ -468,7 +468,7 @@ def autotune_cache():
 
 
 def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11, reference=None,
-              with_cpu=False, oracle_results=None):
+              with_cpu=False, oracle_results=None, engine="auto"):
     """Batched sweep: `count` independent noisy circuits (n ~ U{4..11}, depth
     ~ U{50..500}, {H, RZ, RX, CX}, per-circuit depolarising p) in one
     persistent launch per run (a CUDA graph replay), tile and fusion width per
@@ -480,9 +480,9 @@ def run_sweep(tq, torch, precision, steps, warmup, count=1024, n_min=4, n_max=11
     from paper_2404_13184_gb300 import workloads
     circuits = workloads.sweep(count, n_min=n_min, n_max=n_max)
     t_tune = time.perf_counter()
-    tuned = {n: tq.autotune(precision, n, autotune_cache()) for n in sorted({c.n for c in circuits})}
+    tuned = {n: tq.autotune(precision, n, autotune_cache(), engine=engine) for n in sorted({c.n for c in circuits})}
     t_tune = time.perf_counter() - t_tune
-    b = tq.Batch(precision)
+    b = tq.Batch(precision, engine=engine)
     for c in circuits:
         b.add(c.n, c.ops, width=tuned[c.n][1], masks=[1, 3])
     for n, (tile, _, _) in tuned.items():
@@ -933,7 +933,8 @@ def main():
     ap.add_argument("--serve-drain-in-line", type=float, default=20.0,
                     help="drain window (s) after the in-line served streams' arrivals stop")
     ap.add_argument("--fp64-engine", default="auto", choices=["auto", "dfma", "tensor"],
-                    help="products of the FP64 apply passes (tq_set_fp64_engine)")
+                    help="products of the FP64 apply passes (tq_set_fp64_engine; the sweep mode's batch: "
+                         "tq_batch_set_fp64_engine)")
     ap.add_argument("--no-dfma-leg", action="store_true",
                     help="leave out the DFMA-engine comparison when the FP64 leg runs on the tensor cores")
     ap.add_argument("--no-extras", action="store_true",
@@ -991,7 +992,8 @@ def main():
                 lo, hi = (int(v) for v in args.sweep_qubits.split("-"))
                 r = run_sweep(tq, torch, prec, args.steps, args.warmup, count=args.sweep_count, n_min=lo, n_max=hi,
                               reference=fp64_results if prec == "split" else None,
-                              with_cpu=prec == precs[0] and rank == 0 and not args.no_cpu_baseline)
+                              with_cpu=prec == precs[0] and rank == 0 and not args.no_cpu_baseline,
+                              engine=args.fp64_engine)
                 res = r.pop("results")
                 r.pop("oracle_results")
                 if prec == "fp64":

@@ -408,6 +408,13 @@ void tq_batch_free(tq_batch* b);
 tq_status tq_autotune(int precision, int n_qubits, const char* cache_path, int* tile_log2_out,
                       int* width_out, double* ms_out);
 
+/* The same for a batch that runs FP64 on the given engine (tq_fp64_engine):
+ * the candidates run on that engine, and FP64 results on the DFMA engine are
+ * cached under "fp64-dfma" (tq_autotune is this call with TQ_ENGINE_AUTO,
+ * cached under "fp64"). */
+tq_status tq_autotune_engine(int precision, int fp64_engine, int n_qubits, const char* cache_path,
+                             int* tile_log2_out, int* width_out, double* ms_out);
+
 /* ---- serving loop (continuous batching of circuit requests) --------------
  * Requests (independent circuits, each on its own |0..0><0..0|) wait in a
  * FIFO queue. A request is admitted, in order, when its density matrix fits

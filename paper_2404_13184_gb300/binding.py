@@ -93,6 +93,8 @@ _SIGNATURES = [
     ("tq_batch_work", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     ("tq_batch_free", None, [c_void_p]),
     ("tq_autotune", c_int, [c_int, c_int, ctypes.c_char_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)]),
+    ("tq_autotune_engine", c_int, [c_int, c_int, c_int, ctypes.c_char_p, POINTER(c_int), POINTER(c_int),
+                                   POINTER(c_double)]),
     ("tq_server_create", c_int, [c_int, c_void_p, c_size_t, c_size_t, c_int, POINTER(c_void_p)]),
     ("tq_server_submit", c_int, [c_void_p, c_int, POINTER(TqOp), c_size_t, c_int, POINTER(c_uint64), c_int,
                                  POINTER(c_int)]),
@@ -291,12 +293,18 @@ class Batch:
             pass
 
 
-def autotune(precision: str, n: int, cache_path: str | None = None):
-    """(tile_log2, fusion width, ms per run) for the batch engine at n qubits."""
+def autotune(precision: str, n: int, cache_path: str | None = None, engine: str = "auto"):
+    """(tile_log2, fusion width, ms per run) for the batch engine at n qubits
+    (FP64: on the given engine)."""
     lib = load()
     t, w, ms = c_int(0), c_int(0), c_double(0)
-    _check(lib.tq_autotune(PRECISION[precision], n, cache_path.encode() if cache_path else None, ctypes.byref(t),
-                           ctypes.byref(w), ctypes.byref(ms)), "tq_autotune")
+    path = cache_path.encode() if cache_path else None
+    if engine == "auto":
+        _check(lib.tq_autotune(PRECISION[precision], n, path, ctypes.byref(t), ctypes.byref(w), ctypes.byref(ms)),
+               "tq_autotune")
+    else:
+        _check(lib.tq_autotune_engine(PRECISION[precision], ENGINES[engine], n, path, ctypes.byref(t),
+                                      ctypes.byref(w), ctypes.byref(ms)), "tq_autotune_engine")
     return t.value, w.value, ms.value
 
 

@@ -15,6 +15,10 @@
 #include "tq_internal.h"
 #include <cuda_runtime.h>
 
+namespace tq {
+bool fp64_engine_is_tensor(int engine);  // tq_state.cu
+}
+
 namespace {
 
 // splitmix64: the tuner's own workload generator (not a parity input)
@@ -63,7 +67,7 @@ std::vector<tq_op> synth_circuit(int n, int depth, Rng& rng) {
   return ops;
 }
 
-std::string cache_key(int precision, int n) {
+std::string cache_key(int precision, int dfma, int n) {
   cudaDeviceProp prop;
   int dev = 0;
   std::string name = "unknown";
@@ -71,7 +75,7 @@ std::string cache_key(int precision, int n) {
   for (char& c : name)
     if (c == ' ') c = '_';
   std::ostringstream os;
-  os << name << " " << (precision == TQ_FP64 ? "fp64" : "split") << " " << n;
+  os << name << " " << (precision == TQ_FP64 ? (dfma ? "fp64-dfma" : "fp64") : "split") << " " << n;
   return os.str();
 }
 
@@ -97,12 +101,15 @@ bool cache_lookup(const char* path, const std::string& key, int* tile, int* widt
 
 }  // namespace
 
-extern "C" tq_status tq_autotune(int precision, int n_qubits, const char* cache_path, int* tile_log2_out,
-                                 int* width_out, double* ms_out) {
+extern "C" tq_status tq_autotune_engine(int precision, int fp64_engine, int n_qubits, const char* cache_path,
+                                        int* tile_log2_out, int* width_out, double* ms_out) {
   if ((precision != TQ_FP64 && precision != TQ_SPLIT) || n_qubits < 2 || n_qubits > 14 || !tile_log2_out ||
-      !width_out)
+      !width_out || fp64_engine < TQ_ENGINE_AUTO || fp64_engine > TQ_ENGINE_TENSOR)
     return TQ_ERR_ARG;
-  const std::string key = cache_key(precision, n_qubits);
+  // FP64 batches tune on the engine they will run with (the tile size only
+  // matters on the DFMA engine's persistent kernel)
+  const int dfma = precision == TQ_FP64 && !tq::fp64_engine_is_tensor(fp64_engine);
+  const std::string key = cache_key(precision, dfma, n_qubits);
   int tile = 0, width = 0;
   double best_ms = 0;
   if (cache_lookup(cache_path, key, &tile, &width, &best_ms)) {
@@ -139,6 +146,7 @@ extern "C" tq_status tq_autotune(int precision, int n_qubits, const char* cache_
     for (int t : tiles) {
       tq_batch* b = nullptr;
       tq_status s = tq_batch_create(precision, st, &b);
+      if (s == TQ_OK && precision == TQ_FP64) s = tq_batch_set_fp64_engine(b, fp64_engine);
       for (int j = 0; j < jobs && s == TQ_OK; ++j)
         s = tq_batch_add(b, n_qubits, circuits[j].data(), circuits[j].size(), w, nullptr, 0, nullptr);
       if (s == TQ_OK) s = tq_batch_set_tile(b, n_qubits, t);
@@ -177,4 +185,9 @@ extern "C" tq_status tq_autotune(int precision, int n_qubits, const char* cache_
     f << key << " " << tile << " " << width << " " << std::setprecision(17) << best_ms << "\n";
   }
   return TQ_OK;
+}
+
+extern "C" tq_status tq_autotune(int precision, int n_qubits, const char* cache_path, int* tile_log2_out,
+                                 int* width_out, double* ms_out) {
+  return tq_autotune_engine(precision, TQ_ENGINE_AUTO, n_qubits, cache_path, tile_log2_out, width_out, ms_out);
 }

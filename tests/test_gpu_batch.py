@@ -268,6 +268,11 @@ def test_autotune_picks_a_valid_candidate_and_caches(tq, tmp_path):
     assert len(lines) == 1 and lines[0].split()[1:3] == ["fp64", "8"]
     assert tq.autotune("fp64", 8, cache) == (t, w, ms)          # answered from the cache
     assert len(open(cache).read().splitlines()) == 1
+    # the DFMA engine is tuned on its own and cached under its own key
+    td, wd, msd = tq.autotune("fp64", 8, cache, engine="dfma")
+    assert wd in (1, 2) and 4 <= td <= 16 and msd > 0
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 2 and lines[1].split()[1:3] == ["fp64-dfma", "8"]
     # the tuned settings give the same results as the defaults
     jobs = _jobs(5, 8, 8, 11)
     a, b = tq.Batch("fp64"), tq.Batch("fp64")
