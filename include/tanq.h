@@ -337,17 +337,22 @@ tq_status tq_batch_add(tq_batch* b, int n_qubits, const tq_op* ops, size_t n_ops
  * granularity of the persistent kernel, normally set by the autotuner. */
 tq_status tq_batch_set_tile(tq_batch* b, int n_qubits, int tile_log2);
 
-/* FP64 engine of the batch's tile jobs (vec(rho) > 64 KiB), as for single
- * states (tq_fp64_engine; default TQ_ENGINE_AUTO). With the tensor-core
- * engine, a tile job whose blocks are all of width <= 2 on at least 6
- * qubits runs on the batched FP64-accurate tensor-core pass instead of the
+/* Engine of the batch's tile jobs (vec(rho) > 64 KiB; tq_fp64_engine,
+ * default TQ_ENGINE_AUTO). On the batched tensor-core pass of its precision
+ * a tile job whose blocks are all of width <= 2 runs instead of on the
  * persistent kernel: one launch per fusion round, each applying that
- * round's block of every such job (tq_set_fp64_engine describes the
- * arithmetic). Resident jobs and split batches are unaffected. Takes effect
- * at the next run. */
+ * round's block of every such job (FP64: the FP64-accurate digit pass
+ * tq_set_fp64_engine describes; split: the three-term BF16 pass of single
+ * split states; width-1 blocks as S (x) I). FP64 takes it with
+ * TQ_ENGINE_AUTO or TQ_ENGINE_TENSOR, split only with TQ_ENGINE_TENSOR (the
+ * faster choice measured on GB300 in each precision; the split pass is the
+ * more accurate one). Otherwise the persistent kernel runs every job (FP64
+ * DFMA row lists; split FP32 Pauli-basis products on the CUDA cores).
+ * Resident jobs always run on the persistent kernel. Takes effect at the
+ * next run. */
 tq_status tq_batch_set_fp64_engine(tq_batch* b, int engine);
 
-/* Jobs of the last planned run that ran on the batched tensor-core pass. */
+/* Jobs of the last planned run on a batched tensor-core pass. */
 tq_status tq_batch_tensor_jobs(const tq_batch* b, size_t* n_jobs);
 
 /* Enqueue one run of every job (asynchronous). */
@@ -386,8 +391,8 @@ tq_status tq_batch_info(const tq_batch* b, size_t* n_jobs, size_t* n_items, size
  * jobs that the kernel runs in the Pauli basis (real R' = T S T^dagger /
  * 16): FP64 row lists of R' count 4 flops per nonzero plus the 128 adds of
  * the basis changes, split (always in the Pauli basis, R' dense) 4 x 256 +
- * 128; blocks of jobs on the tensor-core pass count the dense product (8
- * per entry of S). bytes: what the apply passes must move through
+ * 128; blocks of jobs on a batched tensor-core pass count the dense
+ * product (8 per entry of S). bytes: what the apply passes must move through
  * HBM: per block of a tile job one read and one write of the stored entries
  * (the upper triangle in Hermitian mode), per resident job one load and one
  * store of vec(rho). TQ_ERR_STATE before the first run; waits for the run. */
@@ -408,10 +413,10 @@ void tq_batch_free(tq_batch* b);
 tq_status tq_autotune(int precision, int n_qubits, const char* cache_path, int* tile_log2_out,
                       int* width_out, double* ms_out);
 
-/* The same for a batch that runs FP64 on the given engine (tq_fp64_engine):
- * the candidates run on that engine, and FP64 results on the DFMA engine are
- * cached under "fp64-dfma" (tq_autotune is this call with TQ_ENGINE_AUTO,
- * cached under "fp64"). */
+/* The same for a batch that runs on the given engine (tq_fp64_engine, as
+ * tq_batch_set_fp64_engine): the candidates run on that engine; results are
+ * cached under "fp64" (tensor-core pass), "fp64-dfma", "split" (persistent
+ * kernel) or "split-tc" (tq_autotune is this call with TQ_ENGINE_AUTO). */
 tq_status tq_autotune_engine(int precision, int fp64_engine, int n_qubits, const char* cache_path,
                              int* tile_log2_out, int* width_out, double* ms_out);
 

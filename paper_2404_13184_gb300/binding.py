@@ -227,11 +227,11 @@ class Batch:
             self.set_fp64_engine(engine)
 
     def set_fp64_engine(self, engine: str):
-        """FP64 engine of the tile jobs: "auto" (tensor cores), "dfma" or "tensor"."""
+        """Engine of the tile jobs: "auto" / "tensor" (tensor cores) or "dfma" (the persistent kernel)."""
         _check(_lib.tq_batch_set_fp64_engine(self._h, ENGINES[engine]), "tq_batch_set_fp64_engine")
 
     def tensor_jobs(self) -> int:
-        """Jobs of the last planned run on the batched tensor-core pass."""
+        """Jobs of the last planned run on a batched tensor-core pass."""
         v = c_size_t(0)
         _check(_lib.tq_batch_tensor_jobs(self._h, ctypes.byref(v)), "tq_batch_tensor_jobs")
         return v.value

@@ -69,7 +69,7 @@
 #include "tq_device.cuh"
 #include "tanq.h"
 #include "tq_tc.cuh"
-#include "tq_oz.cuh"
+#include "tq_batched.cuh"
 
 namespace tq {
 

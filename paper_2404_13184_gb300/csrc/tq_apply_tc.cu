@@ -28,6 +28,7 @@
 #include "tq_device.cuh"
 #include "tanq.h"
 #include "tq_tc.cuh"
+#include "tq_batched.cuh"
 
 namespace tq {
 
@@ -197,6 +198,150 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_apply_herm_tc2(float2*
   }
 }
 
+// Batched form of the pass: one fusion round of many independent split
+// states (the batch engine's split tile jobs), from a table of (state,
+// block) jobs whose units are numbered one after another. Each CTA takes a
+// contiguous range of units; where the range crosses into the next job it
+// switches to that job's index tables, rebuilds the B operand (the previous
+// unit's MMAs completed before any thread left its wait, and the epilogue
+// does not read B) and loads the job's first unit without prefetch. The
+// per-unit work is the single-state pass's.
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_batch_tc2(const TcJob* __restrict__ jobs, int n_jobs,
+                                                                      unsigned long long n_units_total,
+                                                                      unsigned long long chunk, long long max_tries,
+                                                                      int skip_mma) {
+  constexpr int D = 16;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t bar = sbase + kOffBar;
+  volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(smem + kOffTmem);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kOffFlag);
+  const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+  if (tid == 0) {
+    bar_init(bar, 1);
+    *s_abort = 0;
+  }
+  if (w == 0) tmem_alloc(sbase + kOffTmem, kTmemCols);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  const int i = (lane % 8) + 8 * (w % 2), j0 = (lane / 8) + 4 * (w / 2);
+  const uint32_t a_row = sbase + kOffA + core_off(tid, 0);
+  const uint32_t t_row = tmem + ((uint32_t)(32 * w) << 16);
+
+  // the current job's tables
+  int jn = 0;
+  float2* rho = nullptr;
+  unsigned int b0 = 0, b1 = 0, N = 0, di = 0, dj0 = 0, dj1 = 0;
+  int qs[2] = {0, 0};
+  unsigned long long ubase = 0;
+  auto set_job = [&](unsigned long long uu) {
+    while (jn + 1 < n_jobs && jobs[jn + 1].unit0 <= uu) ++jn;
+    const TcJob& J = jobs[jn];
+    rho = J.rho;
+    qs[0] = min(J.p.q[0], J.p.q[1]);
+    qs[1] = max(J.p.q[0], J.p.q[1]);
+    b0 = 1u << J.p.q[0];
+    b1 = 1u << J.p.q[1];
+    N = 1u << J.p.n;
+    di = (unsigned int)deposit_zeros(i, qs, 2);
+    dj0 = (unsigned int)deposit_zeros(j0, qs, 2);
+    dj1 = (unsigned int)deposit_zeros(j0 + 8, qs, 2);
+    ubase = J.unit0;
+  };
+  auto same_job = [&](unsigned long long uu) { return jn + 1 >= n_jobs || jobs[jn + 1].unit0 > uu; };
+  auto group_of = [&](unsigned long long uu) {
+    const unsigned long long v = uu - ubase;
+    bool diag = false;
+    const unsigned long long tt = canonical_group(v >> 1, 32, &diag);
+    const int j = (int)(v & 1ull) * 8 + j0;
+    Group g;
+    g.active = !(diag && i > j);
+    g.self = diag && i == j;
+    g.rb = (unsigned int)deposit_zeros((tt & 0xffffffffull) * kTile, qs, 2) + di;
+    g.cb = (unsigned int)deposit_zeros((tt >> 32) * kTile, qs, 2) + ((v & 1ull) ? dj1 : dj0);
+    return g;
+  };
+  auto load = [&](const Group& g, float2 x[D]) {
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      bool up;
+      const unsigned int idx = entry_index(g.rb, g.cb, l, b0, b1, N, &up);
+      x[l] = g.active ? rho[idx] : make_float2(0.f, 0.f);
+    }
+  };
+
+  unsigned long long u = (unsigned long long)blockIdx.x * chunk;
+  const unsigned long long u_end = min(u + chunk, n_units_total);
+  Group gn{};
+  float2 xn[D];
+  bool have = false;
+  uint32_t phase = 0;
+#pragma unroll 1
+  for (; u < u_end; ++u, phase ^= 1u) {
+    if (!have) {  // first unit, or the first unit of the next job
+      set_job(u);
+      build_b(smem + kOffB, jobs[jn].S, tid, kThreads, jobs[jn].embed);
+      gn = group_of(u);
+      load(gn, xn);
+    }
+    const Group g = gn;
+    float2 x[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) x[l] = xn[l];
+    have = u + 1 < u_end && same_job(u + 1);
+    if (have) {
+      gn = group_of(u + 1);
+      load(gn, xn);
+    }
+    store_row(x, g.rb, g.cb, b0, b1, N, a_row, kATermBytes);
+    fence_operands();
+    fence_before_sync();
+    __syncthreads();
+    if (*s_abort) break;
+    if (tid == 0 && !skip_mma) {
+      fence_after_sync();
+      mma_split3(tmem, sbase + kOffA, kATermBytes, sbase + kOffB, kBTermBytes);
+      commit(bar);
+    }
+    const bool waited = bar_wait(bar, phase, max_tries);
+    if (!waited) {
+      atomicAdd(&g_tc_timeouts, 1u);
+      *s_abort = 1;
+    }
+    if (!__all_sync(0xffffffffu, waited)) continue;
+    fence_after_sync();
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float dv[16];
+      tmem_ld16(t_row + hh * 16, dv);
+      if (!g.active) continue;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int o = hh * 8 + q;
+        bool up;
+        const unsigned int idx = entry_index(g.rb, g.cb, o, b0, b1, N, &up);
+        float2 y = make_float2(x[o].x + dv[2 * q], x[o].y + dv[2 * q + 1]);
+        if (up) {
+          rho[idx] = y;
+        } else if (!g.self) {
+          y.y = -y.y;
+          rho[idx] = y;
+        }
+      }
+    }
+    fence_before_sync();
+  }
+  __syncthreads();
+  if (*s_abort && tid == 0) bar_wait(bar, phase ^ 1u, max_tries);
+  __syncthreads();
+  if (w == 0) {
+    fence_after_sync();
+    tmem_free(tmem, kTmemCols);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_herm_tc2(float2* rho, const float2* S, const ApplyParams& p, int num_sms, cudaStream_t st) {
@@ -214,6 +359,43 @@ cudaError_t launch_herm_tc2(float2* rho, const float2* S, const ApplyParams& p, 
   const int grid = (int)std::max<unsigned long long>(
       1, std::min<unsigned long long>(n_units, (unsigned long long)num_sms * kCtasPerSm));
   k_apply_herm_tc2<<<grid, kThreads, kSmemBytes, st>>>(rho, S, p, g_test_max_tries.load(), g_test_skip_mma.load());
+  return cudaGetLastError();
+}
+
+unsigned long long tc_units(int n) {
+  const unsigned long long Mt = (1ull << (n - 2)) / kTile;
+  return Mt * (Mt + 1);
+}
+
+bool tc_job(float2* rho, const float2* S, const ApplyParams& p, TcJob* out) {
+  if ((p.width != 1 && p.width != 2) || p.n - 2 < 4) return false;
+  TcJob j{};
+  j.rho = rho;
+  j.S = S;
+  j.p = p;
+  if (p.width == 1) {  // S (x) I on (q, q'), q' the highest other qubit
+    j.embed = 1;
+    j.p.width = 2;
+    j.p.q[1] = p.q[0] == p.n - 1 ? p.n - 2 : p.n - 1;
+  }
+  *out = j;
+  return true;
+}
+
+cudaError_t launch_batch_tc(const TcJob* jobs, int n_jobs, unsigned long long n_units, int num_sms,
+                            cudaStream_t st) {
+  if (n_jobs <= 0 || n_units == 0) return cudaSuccess;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(k_batch_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  });
+  if (attr != cudaSuccess) return attr;
+  const unsigned long long slots = (unsigned long long)num_sms * kCtasPerSm;
+  const unsigned long long chunk = (n_units + slots - 1) / slots;
+  const int grid = (int)((n_units + chunk - 1) / chunk);
+  k_batch_tc2<<<grid, kThreads, kSmemBytes, st>>>(jobs, n_jobs, n_units, chunk, g_test_max_tries.load(),
+                                                  g_test_skip_mma.load());
   return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@
 #include <cuda_runtime.h>
 
 namespace tq {
-bool fp64_engine_is_tensor(int engine);  // tq_state.cu
+bool batch_tensor_engine(int precision, int engine);  // tq_batch.cu
 }
 
 namespace {
@@ -67,7 +67,7 @@ std::vector<tq_op> synth_circuit(int n, int depth, Rng& rng) {
   return ops;
 }
 
-std::string cache_key(int precision, int dfma, int n) {
+std::string cache_key(int precision, int tensor, int n) {
   cudaDeviceProp prop;
   int dev = 0;
   std::string name = "unknown";
@@ -75,7 +75,8 @@ std::string cache_key(int precision, int dfma, int n) {
   for (char& c : name)
     if (c == ' ') c = '_';
   std::ostringstream os;
-  os << name << " " << (precision == TQ_FP64 ? (dfma ? "fp64-dfma" : "fp64") : "split") << " " << n;
+  os << name << " " << (precision == TQ_FP64 ? (tensor ? "fp64" : "fp64-dfma") : (tensor ? "split-tc" : "split")) << " "
+     << n;
   return os.str();
 }
 
@@ -106,10 +107,10 @@ extern "C" tq_status tq_autotune_engine(int precision, int fp64_engine, int n_qu
   if ((precision != TQ_FP64 && precision != TQ_SPLIT) || n_qubits < 2 || n_qubits > 14 || !tile_log2_out ||
       !width_out || fp64_engine < TQ_ENGINE_AUTO || fp64_engine > TQ_ENGINE_TENSOR)
     return TQ_ERR_ARG;
-  // FP64 batches tune on the engine they will run with (the tile size only
-  // matters on the DFMA engine's persistent kernel)
-  const int dfma = precision == TQ_FP64 && !tq::fp64_engine_is_tensor(fp64_engine);
-  const std::string key = cache_key(precision, dfma, n_qubits);
+  // batches tune on the engine they will run with (the tile size only
+  // matters on the persistent kernel)
+  const int tensor = tq::batch_tensor_engine(precision, fp64_engine) ? 1 : 0;
+  const std::string key = cache_key(precision, tensor, n_qubits);
   int tile = 0, width = 0;
   double best_ms = 0;
   if (cache_lookup(cache_path, key, &tile, &width, &best_ms)) {
@@ -146,7 +147,7 @@ extern "C" tq_status tq_autotune_engine(int precision, int fp64_engine, int n_qu
     for (int t : tiles) {
       tq_batch* b = nullptr;
       tq_status s = tq_batch_create(precision, st, &b);
-      if (s == TQ_OK && precision == TQ_FP64) s = tq_batch_set_fp64_engine(b, fp64_engine);
+      if (s == TQ_OK) s = tq_batch_set_fp64_engine(b, fp64_engine);
       for (int j = 0; j < jobs && s == TQ_OK; ++j)
         s = tq_batch_add(b, n_qubits, circuits[j].data(), circuits[j].size(), w, nullptr, 0, nullptr);
       if (s == TQ_OK) s = tq_batch_set_tile(b, n_qubits, t);

@@ -10,7 +10,7 @@
 #include <vector>
 
 #include "tq_batch_kernels.cuh"
-#include "tq_oz.cuh"
+#include "tq_batched.cuh"
 
 using namespace tq;
 using namespace tq::batch;
@@ -36,8 +36,8 @@ struct tq_batch {
   DevBuf arena, blob, sops, sb64, sb32, djobs, dblks, ditems, counters, ctl, results;
   DevBuf pauli, pwork;  // Pauli-basis records of width-2 tile-job blocks and their sb64 offsets
   int n_pauli = 0;
-  // FP64 tile jobs on the batched tensor-core pass: one launch per fusion
-  // round over every such job's block of that round
+  // tile jobs on the batched tensor-core pass of their precision: one
+  // launch per fusion round over every such job's block of that round
   int fp64_engine = TQ_ENGINE_AUTO;
   struct OzRound {
     size_t off;
@@ -55,6 +55,20 @@ struct tq_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<unsigned long long> rho_off;
 };
+
+namespace tq {
+
+// Whether a batch's tile jobs take the batched tensor-core pass. FP64: with
+// the tensor-core engine (the default; 3,536 against 1,781 circuits/s on the
+// 1024-circuit sweep). Split: only when TQ_ENGINE_TENSOR is asked for; the
+// default keeps the persistent kernel, measured faster on the same sweep
+// (11,381 against 10,900 circuits/s; its rounds cannot share SMs with the
+// persistent kernel, and small registers have few units per round).
+bool batch_tensor_engine(int precision, int engine) {
+  return precision == TQ_FP64 ? fp64_engine_is_tensor(engine) : engine == TQ_ENGINE_TENSOR;
+}
+
+}  // namespace tq
 
 namespace {
 
@@ -176,11 +190,12 @@ tq_status finalize(tq_batch* b) {
     // at least 16 groups' worth of entries per tile, at most 2^16 tiles per block
     hj.tile_log2 = std::min(std::max({tl, 4, 2 * J.n - 16}), 2 * J.n);
     hj.herm = batch_herm(J.n, b->prec) ? 1 : 0;
-    // FP64 tile jobs whose blocks are all eligible run on the batched
-    // tensor-core pass (with the tensor-core engine; a job under the
-    // never-ready test hook stays on the batch kernel, whose waits it tests)
+    // tile jobs whose blocks are all eligible run on the batched tensor-core
+    // pass of their precision when batch_tensor_engine says so (a job under
+    // the never-ready test hook stays on the batch kernel, whose waits it
+    // tests)
     hj.tensor = 0;
-    if (b->prec == TQ_FP64 && fp64_engine_is_tensor(b->fp64_engine) && !hj.resident && (int)j != b->never_ready_job) {
+    if (batch_tensor_engine(b->prec, b->fp64_engine) && !hj.resident && (int)j != b->never_ready_job) {
       bool all = !J.prog.params.empty();
       for (const ApplyParams& pp : J.prog.params) all = all && oz_eligible(pp.n, pp.width);
       hj.tensor = all ? 1 : 0;
@@ -283,6 +298,7 @@ tq_status finalize(tq_batch* b) {
   b->n_tensor_jobs = 0;
   {
     std::vector<OzJob> oz;
+    std::vector<TcJob> tc;
     int rounds = 0;
     for (const BJob& hj : hjobs)
       if (hj.tensor) {
@@ -290,24 +306,33 @@ tq_status finalize(tq_batch* b) {
         rounds = std::max(rounds, hj.n_blocks);
       }
     for (int r = 0; r < rounds; ++r) {
-      tq_batch::OzRound rd{oz.size(), 0, 0};
+      tq_batch::OzRound rd{b->prec == TQ_FP64 ? oz.size() : tc.size(), 0, 0};
       for (size_t j = 0; j < hjobs.size(); ++j) {
         const BJob& hj = hjobs[j];
         if (!hj.tensor || r >= hj.n_blocks) continue;
         const BBlk& bb = hblks[hj.block0 + r];
-        OzJob oj{};
-        oz_job(reinterpret_cast<double2*>(static_cast<char*>(b->arena.ptr) + hj.rho_off),
-               static_cast<const double2*>(bb.S), bb.p, &oj);
-        oj.unit0 = rd.units;
+        char* rho = static_cast<char*>(b->arena.ptr) + hj.rho_off;
+        if (b->prec == TQ_FP64) {
+          OzJob oj{};
+          oz_job(reinterpret_cast<double2*>(rho), static_cast<const double2*>(bb.S), bb.p, &oj);
+          oj.unit0 = rd.units;
+          oz.push_back(oj);
+        } else {
+          TcJob tj{};
+          tc_job(reinterpret_cast<float2*>(rho), static_cast<const float2*>(bb.S), bb.p, &tj);
+          tj.unit0 = rd.units;
+          tc.push_back(tj);
+        }
         rd.units += oz_units(hj.n);
-        oz.push_back(oj);
         ++rd.count;
       }
       b->oz_rounds.push_back(rd);
     }
-    if (e == cudaSuccess) e = alloc(b->ozjobs, std::max<size_t>(1, oz.size()) * sizeof(OzJob));
-    if (e == cudaSuccess && !oz.empty())
-      e = cudaMemcpy(b->ozjobs.ptr, oz.data(), oz.size() * sizeof(OzJob), cudaMemcpyHostToDevice);
+    const size_t bytes = b->prec == TQ_FP64 ? oz.size() * sizeof(OzJob) : tc.size() * sizeof(TcJob);
+    if (e == cudaSuccess) e = alloc(b->ozjobs, std::max<size_t>(16, bytes));
+    if (e == cudaSuccess && bytes)
+      e = cudaMemcpy(b->ozjobs.ptr, b->prec == TQ_FP64 ? (const void*)oz.data() : (const void*)tc.data(), bytes,
+                     cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) return to_status(e);
 
@@ -361,8 +386,12 @@ tq_status finalize(tq_batch* b) {
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
   }
-  for (const tq_batch::OzRound& rd : b->oz_rounds)
-    launch_batch_oz(static_cast<const OzJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, st);
+  for (const tq_batch::OzRound& rd : b->oz_rounds) {
+    if (b->prec == TQ_FP64)
+      launch_batch_oz(static_cast<const OzJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, st);
+    else
+      launch_batch_tc(static_cast<const TcJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, st);
+  }
   if (b->prec == TQ_FP64)
     k_batch_reduce<double2><<<n_jobs, kThreads, 0, st>>>(static_cast<const char*>(b->arena.ptr),
                                                          static_cast<const BJob*>(b->djobs.ptr), 0,
@@ -475,9 +504,11 @@ tq_status tq_batch_wait(tq_batch* b) {
   if (!b->ready) return TQ_OK;
   const int err = *reinterpret_cast<const int*>(static_cast<const char*>(b->host_out.ptr) +
                                                 b->jobs.size() * kResults * sizeof(double));
-  unsigned int oz_timeouts = 0;
-  if (b->n_tensor_jobs && oz_take_timeouts(&oz_timeouts, b->stream) != cudaSuccess) return TQ_ERR_CUDA;
-  return err || oz_timeouts ? TQ_ERR_TIMEOUT : TQ_OK;
+  unsigned int tc_timeouts = 0;
+  if (b->n_tensor_jobs && (b->prec == TQ_FP64 ? oz_take_timeouts(&tc_timeouts, b->stream)
+                                              : tc_take_timeouts(&tc_timeouts, b->stream)) != cudaSuccess)
+    return TQ_ERR_CUDA;
+  return err || tc_timeouts ? TQ_ERR_TIMEOUT : TQ_OK;
 }
 
 tq_status tq_batch_result(tq_batch* b, int job, double* out) {

@@ -1,5 +1,6 @@
-// Batched FP64-accurate tensor-core pass (tq_apply_oz.cu): the job table a
-// launch takes, shared by the kernel and the batch engine that builds it.
+// Batched tensor-core passes (the FP64-accurate pass of tq_apply_oz.cu and
+// the split pass of tq_apply_tc.cu): the job tables a launch takes, shared by
+// the kernels and the batch engine that builds them.
 #pragma once
 
 #include "tq_device.cuh"
@@ -26,6 +27,24 @@ bool oz_job(double2* rho, const double2* S, const ApplyParams& p, OzJob* out);
 
 // One batched pass over jobs[0 .. n_jobs) (device table, n_units in total).
 cudaError_t launch_batch_oz(const OzJob* jobs, int n_jobs, unsigned long long n_units, int num_sms,
+                            cudaStream_t st);
+
+// The same for the split pass (complex64 states, FP32 superoperators).
+struct TcJob {
+  float2* rho;               // the state's vec(rho), Hermitian mode
+  const float2* S;           // the block's fused superoperator (FP32)
+  ApplyParams p;             // width 2 (a width-1 block: q[1] is the embedding qubit)
+  int embed;                 // 1: S is 4 x 4, applied as S (x) I
+  int pad_;
+  unsigned long long unit0;  // first unit of this job in the launch
+};
+
+// Units of one split pass on n qubits (the same half tiles).
+unsigned long long tc_units(int n);
+
+bool tc_job(float2* rho, const float2* S, const ApplyParams& p, TcJob* out);
+
+cudaError_t launch_batch_tc(const TcJob* jobs, int n_jobs, unsigned long long n_units, int num_sms,
                             cudaStream_t st);
 
 }  // namespace tq

@@ -190,14 +190,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
   for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// Entry (o, l) of the 16 x 16 superoperator a width-2 pass applies: S, or
+// S (x) I for a width-1 block S (4 x 4) embedded on local qubit 0 (local
+// index l = r0 + 2 r1 + 4 c0 + 8 c1; the identity acts on qubit 1).
+__device__ __forceinline__ float2 sop_entry_f(const float2* S, int embed, int o, int l) {
+  if (!embed) return S[o * 16 + l];
+  if (((o >> 1) & 1) != ((l >> 1) & 1) || ((o >> 3) & 1) != ((l >> 3) & 1)) return make_float2(0.f, 0.f);
+  return S[((o & 1) | ((o >> 1) & 2)) * 4 + ((l & 1) | ((l >> 1) & 2))];
+}
+
 // B operand of a width-2 block: (R - I) in three BF16 terms at `b` (shared
 // memory, kBTermBytes per term) from the 16 x 16 complex superoperator S
-// (row-major, any memory space); items e = tid, tid + nthreads, ... < 512,
-// item e being the pair (R[n][2l], R[n][2l + 1]) with n = e / 16, l = e % 16.
-__device__ __forceinline__ void build_b(unsigned char* b, const float2* S, int tid, int nthreads) {
+// (row-major, any memory space; embed: S is a width-1 block applied as S (x)
+// I); items e = tid, tid + nthreads, ... < 512, item e being the pair
+// (R[n][2l], R[n][2l + 1]) with n = e / 16, l = e % 16.
+__device__ __forceinline__ void build_b(unsigned char* b, const float2* S, int tid, int nthreads, int embed = 0) {
   for (int e = tid; e < 32 * 16; e += nthreads) {
     const int n = e / 16, l = e % 16, o = n / 2;
-    const float2 s = S[o * 16 + l];
+    const float2 s = sop_entry_f(S, embed, o, l);
     float re, im;
     if ((n & 1) == 0) {  // Re y_o = Sr x_r - Si x_i
       re = s.x;

@@ -107,7 +107,7 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
     width-2 blocks of tile jobs that the kernel runs in the Pauli basis count
     4 per real-times-complex product plus 128: FP64 per nonzero of R' (when
     that is cheaper than 4 per nonzero of S), split always, dense (256).
-    FP64 tile jobs on the batched tensor-core pass (the default engine)
+    FP64 tile jobs on the batched tensor-core pass (the default FP64 engine)
     count the dense product."""
     esz = 16 if precision == "fp64" else 8
     resident = esz * 4 ** n <= 64 * 1024
@@ -119,7 +119,7 @@ def _expected_work(tq, precision, n, ops, width, diagonal_fp64):
         nnz = 4 ** w if (precision == "fp64" and diagonal_fp64) else 16 ** w
         per = 8 * nnz
         if precision == "fp64" and not resident and n >= 6:
-            per = 8 * 16 ** w          # tensor-core pass: the dense algorithmic count
+            per = 8 * 16 ** w          # batched tensor-core pass: the dense algorithmic count
         elif not resident and w == 2:
             if precision == "split":
                 per = 4 * 256 + 128
@@ -286,27 +286,34 @@ def test_autotune_picks_a_valid_candidate_and_caches(tq, tmp_path):
         assert np.array_equal(a.rho(j), b.rho(j))
 
 
-@pytest.mark.parametrize("engine", ["auto", "dfma"])
-def test_fp64_tile_jobs_on_either_engine_match_the_oracle(tq, engine):
-    # tile jobs (7-9 qubits) run on the batched tensor-core pass with the
-    # default engine, on the persistent kernel with "dfma"; resident jobs on
-    # the persistent kernel either way; one job alone equals itself in the mix
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("engine", ["auto", "dfma", "tensor"])
+def test_tile_jobs_on_either_engine_match_the_oracle(tq, precision, engine):
+    # tile jobs (7-9 qubits) run on the batched tensor-core pass (FP64: auto
+    # or tensor; split: tensor), otherwise on the persistent kernel; resident
+    # jobs on the persistent kernel always; one job alone equals itself in
+    # the mix
     jobs = _jobs(12, 4, 9, 13, depth=(20, 60))
-    b = tq.Batch("fp64", engine=engine)
+    esz = 16 if precision == "fp64" else 8
+    tol = TOL64 if precision == "fp64" else 2e-6
+    ztol = TOL64 if precision == "fp64" else 1e-5
+    b = tq.Batch(precision, engine=engine)
     for n, ops, masks in jobs:
         b.add(n, ops, width=-1, masks=masks)
     b.run()
     b.wait()
-    tiles = sum(1 for n, _, _ in jobs if 16 * 4 ** n > 64 * 1024)
-    assert b.tensor_jobs() == (tiles if engine == "auto" else 0)
+    tiles = sum(1 for n, _, _ in jobs if esz * 4 ** n > 64 * 1024)
+    on_tensor = engine == "tensor" or (engine == "auto" and precision == "fp64")
+    assert b.tensor_jobs() == (tiles if on_tensor else 0)
     for j, (n, ops, masks) in enumerate(jobs):
         want = O.run_circuit(n, ops)
-        assert np.max(np.abs(b.rho(j) - want)) < TOL64, (j, n)
+        assert np.max(np.abs(b.rho(j) - want)) < tol, (j, n)
         res = b.result(j)
         for i, m in enumerate(masks):
-            assert abs(res[2 + i] - O.expect_z(want, m)) < TOL64
-    k = next(j for j, (n, _, _) in enumerate(jobs) if 16 * 4 ** n > 64 * 1024)
-    alone = tq.Batch("fp64", engine=engine)
+            wz = O.expect_z(want, m) / (1.0 if precision == "fp64" else O.trace(want).real)
+            assert abs(res[2 + i] - wz) < ztol
+    k = next(j for j, (n, _, _) in enumerate(jobs) if esz * 4 ** n > 64 * 1024)
+    alone = tq.Batch(precision, engine=engine)
     alone.add(jobs[k][0], jobs[k][1], width=-1, masks=jobs[k][2])
     alone.run()
     alone.wait()
