@@ -26,6 +26,8 @@ struct tq_batch {
   int prec = 0;
   cudaStream_t stream = nullptr;   // where the graph is launched (the caller's)
   cudaStream_t capture = nullptr;  // private stream the graph is captured on
+  cudaStream_t capture2 = nullptr;  // second branch of the graph: the tensor-core rounds
+  cudaEvent_t fork = nullptr, join = nullptr;
   int num_sms = 152;
   int per_sm = 1;
   std::vector<BatchJob> jobs;
@@ -373,6 +375,14 @@ tq_status finalize(tq_batch* b) {
   }
   cudaMemsetAsync(b->counters.ptr, 0, n_jobs * sizeof(int), st);
   cudaMemsetAsync(b->ctl.ptr, 0, 256, st);
+  // the tensor-core rounds are a second branch of the graph, beside the
+  // persistent kernel (they hold other jobs): CTAs of the rounds take the SMs
+  // that the persistent kernel's CTAs leave when its items run out
+  const bool branch = !b->oz_rounds.empty();
+  if (branch) {
+    cudaEventRecord(b->fork, st);
+    cudaStreamWaitEvent(b->capture2, b->fork, 0);
+  }
   const int grid = (int)std::max<size_t>(1, std::min<size_t>(b->n_items, (size_t)b->num_sms * b->per_sm));
   if (b->n_items > 0) {
     if (b->prec == TQ_FP64)
@@ -388,9 +398,13 @@ tq_status finalize(tq_batch* b) {
   }
   for (const tq_batch::OzRound& rd : b->oz_rounds) {
     if (b->prec == TQ_FP64)
-      launch_batch_oz(static_cast<const OzJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, st);
+      launch_batch_oz(static_cast<const OzJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, b->capture2);
     else
-      launch_batch_tc(static_cast<const TcJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, st);
+      launch_batch_tc(static_cast<const TcJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, b->capture2);
+  }
+  if (branch) {
+    cudaEventRecord(b->join, b->capture2);
+    cudaStreamWaitEvent(st, b->join, 0);
   }
   if (b->prec == TQ_FP64)
     k_batch_reduce<double2><<<n_jobs, kThreads, 0, st>>>(static_cast<const char*>(b->arena.ptr),
@@ -427,7 +441,14 @@ tq_status tq_batch_create(int precision, void* cuda_stream, tq_batch** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->capture2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
+    if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->capture2) cudaStreamDestroy(b->capture2);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     delete b;
     return TQ_ERR_CUDA;
   }
@@ -580,6 +601,9 @@ void tq_batch_free(tq_batch* b) {
     if (d->ptr) cudaFree(d->ptr);
   if (b->host_out.ptr) cudaFreeHost(b->host_out.ptr);
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->capture2) cudaStreamDestroy(b->capture2);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   delete b;
 }
 
