@@ -62,6 +62,9 @@
 // Width-1 blocks run through the same kernel as a width-2 block with the
 // identity on a second qubit (S (x) I, built while slicing R), which moves
 // the same number of bytes as a width-1 Hermitian pass.
+//
+// k_batch_oz2 is the same pass over one fusion round of many states (the
+// batch engine's FP64 tile jobs), from a job table (tq_batched.cuh).
 #include <algorithm>
 #include <atomic>
 #include <mutex>

@@ -21,6 +21,10 @@
 //   - every thread waits (bounded) for the MMAs, reads its row of D, adds x
 //     and stores. Groups are disjoint, so the early loads of unit t + 1
 //     never see an entry that unit t writes.
+//
+// k_batch_tc2 is the same pass over one fusion round of many split states
+// (the batch engine's split tile jobs with TQ_ENGINE_TENSOR), from a job
+// table (tq_batched.cuh); width-1 blocks there run as S (x) I.
 #include <algorithm>
 #include <atomic>
 #include <mutex>
