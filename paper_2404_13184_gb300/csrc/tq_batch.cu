@@ -41,13 +41,13 @@ struct tq_batch {
   // tile jobs on the batched tensor-core pass of their precision: one
   // launch per fusion round over every such job's block of that round
   int fp64_engine = TQ_ENGINE_AUTO;
-  struct OzRound {
+  struct PassRound {
     size_t off;
     int count;
     unsigned long long units;
   };
-  DevBuf ozjobs;
-  std::vector<OzRound> oz_rounds;
+  DevBuf pass_jobs;
+  std::vector<PassRound> rounds;
   size_t n_tensor_jobs = 0;
   PinBuf host_out;  // results + error flag
   size_t n_items = 0;
@@ -296,7 +296,7 @@ tq_status finalize(tq_batch* b) {
   if (e == cudaSuccess && !rec_sb.empty())
     e = cudaMemcpy(b->pwork.ptr, rec_sb.data(), rec_sb.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
   // the tensor-core rounds: round r holds block r of every tensor job that has one
-  b->oz_rounds.clear();
+  b->rounds.clear();
   b->n_tensor_jobs = 0;
   {
     std::vector<OzJob> oz;
@@ -308,7 +308,7 @@ tq_status finalize(tq_batch* b) {
         rounds = std::max(rounds, hj.n_blocks);
       }
     for (int r = 0; r < rounds; ++r) {
-      tq_batch::OzRound rd{b->prec == TQ_FP64 ? oz.size() : tc.size(), 0, 0};
+      tq_batch::PassRound rd{b->prec == TQ_FP64 ? oz.size() : tc.size(), 0, 0};
       for (size_t j = 0; j < hjobs.size(); ++j) {
         const BJob& hj = hjobs[j];
         if (!hj.tensor || r >= hj.n_blocks) continue;
@@ -328,12 +328,12 @@ tq_status finalize(tq_batch* b) {
         rd.units += oz_units(hj.n);
         ++rd.count;
       }
-      b->oz_rounds.push_back(rd);
+      b->rounds.push_back(rd);
     }
     const size_t bytes = b->prec == TQ_FP64 ? oz.size() * sizeof(OzJob) : tc.size() * sizeof(TcJob);
-    if (e == cudaSuccess) e = alloc(b->ozjobs, std::max<size_t>(16, bytes));
+    if (e == cudaSuccess) e = alloc(b->pass_jobs, std::max<size_t>(16, bytes));
     if (e == cudaSuccess && bytes)
-      e = cudaMemcpy(b->ozjobs.ptr, b->prec == TQ_FP64 ? (const void*)oz.data() : (const void*)tc.data(), bytes,
+      e = cudaMemcpy(b->pass_jobs.ptr, b->prec == TQ_FP64 ? (const void*)oz.data() : (const void*)tc.data(), bytes,
                      cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) return to_status(e);
@@ -378,7 +378,7 @@ tq_status finalize(tq_batch* b) {
   // the tensor-core rounds are a second branch of the graph, beside the
   // persistent kernel (they hold other jobs): CTAs of the rounds take the SMs
   // that the persistent kernel's CTAs leave when its items run out
-  const bool branch = !b->oz_rounds.empty();
+  const bool branch = !b->rounds.empty();
   if (branch) {
     cudaEventRecord(b->fork, st);
     cudaStreamWaitEvent(b->capture2, b->fork, 0);
@@ -396,11 +396,11 @@ tq_status finalize(tq_batch* b) {
           static_cast<const BBlk*>(b->dblks.ptr), static_cast<const BItem*>(b->ditems.ptr), (int)b->n_items,
           counters, ticket, err, b->max_spin);
   }
-  for (const tq_batch::OzRound& rd : b->oz_rounds) {
+  for (const tq_batch::PassRound& rd : b->rounds) {
     if (b->prec == TQ_FP64)
-      launch_batch_oz(static_cast<const OzJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, b->capture2);
+      launch_batch_oz(static_cast<const OzJob*>(b->pass_jobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, b->capture2);
     else
-      launch_batch_tc(static_cast<const TcJob*>(b->ozjobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, b->capture2);
+      launch_batch_tc(static_cast<const TcJob*>(b->pass_jobs.ptr) + rd.off, rd.count, rd.units, b->num_sms, b->capture2);
   }
   if (branch) {
     cudaEventRecord(b->join, b->capture2);
@@ -596,7 +596,7 @@ void tq_batch_free(tq_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
-  for (DevBuf* d : {&b->arena, &b->blob, &b->sops, &b->sb64, &b->sb32, &b->djobs, &b->dblks, &b->ditems, &b->pauli, &b->pwork, &b->ozjobs,
+  for (DevBuf* d : {&b->arena, &b->blob, &b->sops, &b->sb64, &b->sb32, &b->djobs, &b->dblks, &b->ditems, &b->pauli, &b->pwork, &b->pass_jobs,
                     &b->counters, &b->ctl, &b->results})
     if (d->ptr) cudaFree(d->ptr);
   if (b->host_out.ptr) cudaFreeHost(b->host_out.ptr);
