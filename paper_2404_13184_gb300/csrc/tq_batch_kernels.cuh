@@ -525,7 +525,8 @@ __device__ __forceinline__ void apply_tile16(float2* rho, unsigned long long u, 
 // (the PTX prefetch-size qualifier). A tile's reads in one column of rho are
 // 128-byte runs, and the neighbouring canonical tile, usually in flight in
 // another CTA, reads the other half of the block: 11,465 against 11,406
-// circuits/s on the 1024-circuit split sweep, with bitwise-equal results.
+// circuits/s on the 1024-circuit split sweep, with bitwise-equal results
+// (11,525 with the streaming stores of the tile walk below).
 __device__ __forceinline__ float2 ld_cg_l2_256(const float2* a) {
   float2 v;
   asm volatile("ld.global.cg.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(a));
@@ -601,15 +602,18 @@ __device__ __forceinline__ void apply_tiles16_pauli(float2* rho, unsigned long l
     }
     pauli_inv(y);
     if (act) {
+      // streaming stores: the next reader of these entries is the job's next
+      // block, usually many items later, so L2 keeps the blocks the
+      // neighbouring tiles are still reading instead
 #pragma unroll
       for (int o = 0; o < D; ++o) {
         float2 acc = y[o];
         const unsigned r = rb + t.rt[o], c = cb + t.ct[o];
         if (r <= c) {
-          rho[(unsigned long long)r | ((unsigned long long)c << p.n)] = acc;
+          __stcs(&rho[(unsigned long long)r | ((unsigned long long)c << p.n)], acc);
         } else if (!self) {
           acc.y = -acc.y;
-          rho[(unsigned long long)c | ((unsigned long long)r << p.n)] = acc;
+          __stcs(&rho[(unsigned long long)c | ((unsigned long long)r << p.n)], acc);
         }
       }
     }
