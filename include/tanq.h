@@ -182,16 +182,19 @@ tq_status tq_is_hermitian_mode(const tq_state* s, int* active);
  *  TQ_ENGINE_TENSOR  blocks of width <= 2 in Hermitian mode on registers of
  *                    n >= 6 qubits run on the tcgen05 tensor cores: every
  *                    operand (the group's 32 real values, each real row of
- *                    the superoperator) is cut into eight 7-bit digits of a
- *                    56-bit fixed-point number aligned to the largest
- *                    exponent of its group or row; the digit products, on
- *                    BF16 tensor cores, are summed EXACTLY in FP32 per digit
- *                    order (Ozaki-style error-free splitting) and recombined
- *                    in 64-bit integers, so each output carries the error of
- *                    one rounding plus the operands' rounding at 2^-57 of
- *                    their alignment: FP64 accuracy relative to the largest
- *                    entry of its group (the paper's FP64 tensor-core C2
- *                    update, Sec. 3.2, mapped onto the tensor cores this GPU
+ *                    the superoperator) is cut into seven balanced 8-bit
+ *                    digits of a 54-bit fixed-point number aligned to the
+ *                    largest exponent of its group or row; the digit
+ *                    products, on the tensor cores with FP16 operands, are
+ *                    summed EXACTLY in FP32 per digit order (Ozaki-style
+ *                    error-free splitting) for orders 0..7 (orders >= 8,
+ *                    ~2^-53 of order 0, dropped), and recombined in 64-bit
+ *                    integers, so each output carries the operands' rounding
+ *                    at 2^-55 of their alignment, ~2^-53 from the dropped
+ *                    orders and one final rounding: FP64 accuracy relative
+ *                    to the largest entry of its group (the paper's FP64
+ *                    tensor-core C2 update, Sec. 3.2, mapped onto the
+ *                    tensor cores this GPU
  *                    has). A width-1 block runs as S (x) I on two qubits.
  *                    Other blocks use the DFMA kernels.
  *  TQ_ENGINE_AUTO    the library's choice (the default): the tensor cores

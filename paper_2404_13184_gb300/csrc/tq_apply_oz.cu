@@ -2,8 +2,9 @@
 // (tcgen05, sm_103a), Hermitian mode, for single FP64 states: the product
 // y = S x of every canonical group (TANQ-Sim Sec. 3.1, the C2 update; the
 // paper maps it onto FP64 tensor cores in Sec. 3.2) computed from exact
-// integer products on the BF16 tensor cores, in the manner of the
-// Ozaki-Ogita-Oishi error-free splitting of a dot product.
+// integer products on the 16-bit tensor-core path (kind::f16 with FP16
+// operands), in the manner of the Ozaki-Ogita-Oishi error-free splitting of
+// a dot product.
 //
 // Real-ified product (as in tq_tc.cuh, without taking out the identity):
 // Y[m][n] = sum_k X[m][k] R[n][k], with m one of 128 groups, k one of the

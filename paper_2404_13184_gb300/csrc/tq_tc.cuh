@@ -96,7 +96,8 @@ __host__ __device__ constexpr uint32_t idesc_m128_f16(int n) {
   return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// kind::f16 MMA with an explicit instruction descriptor (BF16 or FP16 operands).
+// kind::f16 MMA with an explicit instruction descriptor: BF16 or FP16
+// operands, as the descriptor says (the FP64-accurate pass uses FP16).
 __device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                            uint32_t accumulate) {
   asm volatile(
