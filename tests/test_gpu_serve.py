@@ -181,6 +181,30 @@ def test_submit_rejects_tables_beyond_the_table_budget(tq):
     srv.free()
 
 
+def test_submit_rejects_blocks_wider_than_two_qubits(tq):
+    # the serving loop applies blocks of at most 2 qubits: a fusion width
+    # above 2, or an op on 3 qubits, is refused at submit and queues nothing;
+    # a valid request submitted afterwards still runs
+    srv = tq.Server("fp64", rho_budget=64 << 20, table_budget=16 << 20, max_live=4)
+    c = W.random_noisy_circuit(4, 10, 33)
+    with pytest.raises(tq.TqError) as e:
+        srv.submit(4, c.ops, width=3, masks=[1])
+    assert e.value.status == 7                          # TQ_ERR_UNSUPPORTED
+    U = np.eye(8, dtype=complex)
+    with pytest.raises(tq.TqError) as e:
+        srv.submit(4, [("unitary", [0, 1, 2], [U])], width=2, masks=[1])
+    assert e.value.status == 7
+    rid = srv.submit(4, c.ops, width=2, masks=[1])
+    guard = 0
+    while srv.poll(rid)[0] != 2 and guard < 100:
+        srv.step()
+        guard += 1
+    st, res = srv.poll(rid)
+    want = O.run_circuit(4, c.ops)
+    assert st == 2 and abs(res[2] - O.expect_z(want, 1)) < TOL64
+    srv.free()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "split"])
 def test_large_requests_run_through_single_state_kernels(tq, precision):
     # requests of >= 12 qubits advance by single-state launches (tensor cores:
